@@ -1,0 +1,562 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a published
+test vector, a closed form derived by hand from an equation of the paper, a
+special case that reduces to a textbook or library routine, an exact
+symmetry, or brute force on a tiny input.  Section / equation numbers refer
+to Chuchvara, Barsi, Gotchev, "Fast and Accurate Depth Estimation from
+Sparse Light Fields" (arXiv 1812.06856).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import ndimage
+
+from oracle import oracle as orc
+from paper_1812_06856_gb300 import synth
+import helpers as H
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def make(K, R, t, rgbs, labs, GW, GH, **pover):
+    return orc.Oracle(K, R, t, rgbs, labs, GW, GH, H.params(**pover), threads=2)
+
+
+# ---------------------------------------------------------------------------
+# jitter (Section III-B) and host logic
+# ---------------------------------------------------------------------------
+
+def test_splitmix64_published_vector():
+    vals = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) if l.startswith("0x")]
+    gamma = 0x9E3779B97F4A7C15
+    got = [orc.splitmix64((n * gamma) & 0xFFFFFFFFFFFFFFFF) for n in range(3)]
+    assert got == vals
+
+
+def test_jitter_uniform_in_unit_interval():
+    us = np.array([orc.jitter_u(7, 0, v, s, k) for v in range(2) for s in range(50) for k in range(50)])
+    assert us.min() >= 0.0 and us.max() < 1.0
+    assert abs(us.mean() - 0.5) < 0.02
+    assert len(np.unique(us)) == len(us)
+    # Kolmogorov-Smirnov distance to U(0,1)
+    xs = np.sort(us)
+    ks = np.max(np.abs(xs - (np.arange(len(xs)) + 0.5) / len(xs)))
+    assert ks < 0.03
+
+
+def _golden_kernel():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "kernel_offsets.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        lhs, rhs = line.split("|")
+        a, b, i = map(int, lhs.split())
+        radii = [int(x) for x in rhs.split()]
+        rows.append((a, b, i, radii))
+    return rows
+
+
+RING = [(1, 0), (1, -1), (0, -1), (-1, -1), (-1, 0), (-1, 1), (0, 1), (1, 1)]
+
+
+@pytest.mark.parametrize("row", _golden_kernel())
+def test_kernel_offsets_hand_derived(row):
+    size_init, steps_init, it, radii = row
+    expect = [(0, 0)] + RING + [(dx * r, dy * r) for r in radii for (dx, dy) in RING]
+    got = [tuple(x) for x in orc.kernel_offsets(size_init, steps_init, it)]
+    assert got == expect
+
+
+def test_neighbor_views_3x3_grid():
+    K, R, t = H.parallel_rig([c for r in range(3) for c in range(3)], 100.0, 32, 24,
+                             ys=[r for r in range(3) for c in range(3)])
+    lab = np.zeros((24, 32), np.int32)
+    img = np.zeros((24, 32, 3))
+    o = make(K, R, t, [img] * 9, [lab] * 9, 1, 1)
+    assert list(o.neighbor_views(4)) == [1, 3, 5, 7, 0, 2, 6, 8]
+    assert list(o.neighbor_views(0)) == [1, 3, 4, 2, 6, 5, 7, 8]
+    o4 = orc.Oracle(K, R, t, [img] * 9, [lab] * 9, 1, 1, H.params(max_neighbor_views=4), threads=1)
+    assert list(o4.neighbor_views(0)) == [1, 3, 4, 2]
+
+
+def test_superpixel_csr_and_stats_brute_force():
+    rng = np.random.default_rng(3)
+    W, Hh = 37, 23
+    lab = rng.integers(0, 12, size=(Hh, W)).astype(np.int32)
+    img = rng.uniform(size=(Hh, W, 3))
+    K, R, t = H.parallel_rig([0, 0.1], 50, W, Hh)
+    o = make(K, R, t, [img, img], [lab, lab], 4, 3)
+    st = o.sp_stats(0)
+    assert st["cnt"].sum() == W * Hh
+    for s in range(12):
+        ys, xs = np.nonzero(lab == s)
+        lin = ys * W + xs                                     # row-major order
+        assert np.array_equal(st["pix"][st["off"][s]:st["off"][s + 1]], lin)
+        assert np.allclose(st["cen"][s], [xs.mean(), ys.mean()], rtol=0, atol=1e-12)
+        assert np.allclose(st["col"][s], img[ys, xs].mean(0), rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# plane model and plane-induced homography (Section III-A, III-B)
+# ---------------------------------------------------------------------------
+
+def _random_rig(rng, V, W, Hh, f):
+    K = np.stack([H.K_pinhole(f, W, Hh)] * V)
+    R = np.stack([H.random_rotation(rng, 10.0) for _ in range(V)])
+    C = rng.uniform(-0.3, 0.3, size=(V, 3))
+    t = np.stack([-R[v] @ C[v] for v in range(V)])
+    return K, R, t
+
+
+def test_projection_equals_world_ray_plane_intersection():
+    rng = np.random.default_rng(11)
+    W, Hh, f = 64, 48, 70.0
+    K, R, t = _random_rig(rng, 3, W, Hh, f)
+    lab = H.grid_label_map(W, Hh, 8, 6)
+    img = rng.uniform(size=(Hh, W, 3))
+    o = make(K, R, t, [img] * 3, [lab] * 3, 8, 6)
+    for trial in range(40):
+        v = int(rng.integers(3))
+        k = int(rng.integers(2))
+        i = int(o.neighbor_views(v)[k])
+        n = np.array([rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5), -1.0])
+        n /= np.linalg.norm(n)
+        d = rng.uniform(2, 4)
+        c = rng.uniform([5, 5], [W - 5, Hh - 5])
+        u, vv = rng.uniform(0, W - 1), rng.uniform(0, Hh - 1)
+        ok, got = o.project_pixel(v, k, [d, *n], c, u, vv)
+        # independent route: the plane and the pixel ray in world coordinates
+        Kinv = np.linalg.inv(K[v])
+        Xc_cam = d * (Kinv @ [c[0], c[1], 1.0])
+        Xc_w = R[v].T @ (Xc_cam - t[v])
+        n_w = R[v].T @ n
+        Cv = -R[v].T @ t[v]
+        dw = R[v].T @ (Kinv @ [u, vv, 1.0])
+        lam = n_w @ (Xc_w - Cv) / (n_w @ dw)
+        X = Cv + lam * dw
+        xi = R[i] @ X + t[i]
+        pix = K[i] @ xi
+        assert ok == (lam > 0 and xi[2] > 0)
+        if ok:
+            assert np.allclose(got[:2], pix[:2] / pix[2], rtol=1e-10, atol=1e-9)
+            assert np.isclose(got[2], xi[2], rtol=1e-10)
+
+
+def test_plane_depth_closed_forms():
+    rng = np.random.default_rng(5)
+    W, Hh, f = 64, 48, 70.0
+    K, R, t = H.parallel_rig([0, 0.1], f, W, Hh)
+    lab = H.grid_label_map(W, Hh, 8, 6)
+    img = np.zeros((Hh, W, 3))
+    o = make(K, R, t, [img, img], [lab, lab], 8, 6)
+    for _ in range(10):
+        n = np.array([rng.uniform(-0.6, 0.6), rng.uniform(-0.6, 0.6), -1.0])
+        n /= np.linalg.norm(n)
+        d = rng.uniform(1.5, 4)
+        c = rng.uniform([10, 10], [W - 10, Hh - 10])
+        assert np.isclose(o.plane_depth(0, [d, *n], c, c[0], c[1]), d, rtol=1e-13)
+        # inverse depth is affine in (u, v): second differences vanish
+        g = np.array([[1.0 / o.plane_depth(0, [d, *n], c, u, vv) for u in (20, 21, 22)] for vv in (15, 16, 17)])
+        assert abs(g[0, 0] - 2 * g[0, 1] + g[0, 2]) < 1e-12
+        assert abs(g[0, 0] - 2 * g[1, 0] + g[2, 0]) < 1e-12
+        assert abs(g[0, 0] - g[0, 1] - g[1, 0] + g[1, 1]) < 1e-12
+    # fronto-parallel plane: depth d everywhere
+    assert np.isclose(o.plane_depth(0, [2.5, 0, 0, -1], [30, 20], 3.0, 41.0), 2.5, rtol=1e-14)
+
+
+def test_bilinear_is_scipy_order1_interpolation():
+    rng = np.random.default_rng(2)
+    img = rng.uniform(size=(13, 17, 3))
+    pts = list(zip(rng.uniform(0, 16, 50), rng.uniform(0, 12, 50))) + [(16.0, 12.0), (16.0, 3.3), (0.0, 0.0), (7.25, 12.0)]
+    for x, y in pts:
+        got = orc.bilinear_image(img, x, y)
+        ref = [ndimage.map_coordinates(img[..., ch], [[y], [x]], order=1, mode="nearest")[0] for ch in range(3)]
+        assert np.allclose(got, ref, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# truncated SSD and the sweep (Eq. 1, Eq. 2)
+# ---------------------------------------------------------------------------
+
+def _affine_pair(d_true, W=64, Hh=48, f=60.0, b=0.1):
+    rig = synth.Rig(*H.parallel_rig([0.0, b], f, W, Hh), W, Hh)
+    A = np.array([[0.5, 0.20, 0.15], [0.4, -0.25, 0.10], [0.6, 0.05, -0.30]])
+    plane = synth.PlaneObj(np.array([0, 0, d_true]), np.array([0, 0, -1.0]), np.array([1.0, 0, 0]),
+                           np.array([0, 1.0, 0]), 100.0, 100.0, np.zeros(3), "affine", affine=A)
+    rgb, depth, _ = synth.render(rig, synth.Scene([plane], []))
+    return rig, rgb.numpy()
+
+
+def test_tssd_zero_on_affine_texture_at_true_depth_and_sweep_recovers_bin():
+    # bilinear interpolation is exact on affine images, so the truncated SSD of
+    # the true plane is 0 (up to rounding) and positive at any other depth
+    d_min, d_max, L, k0 = 1.0, 5.0, 32, 13
+    delta = (1 / d_min - 1 / d_max) / L
+    d_true = 1.0 / (1 / d_max + (k0 + 0.5) * delta)
+    rig, rgb = _affine_pair(d_true)
+    W, Hh = rig.W, rig.H
+    lab = H.grid_label_map(W, Hh, 8, 6)
+    o = make(rig.K, rig.R, rig.t, [rgb[0], rgb[1]], [lab, lab], 8, 6,
+             d_min=d_min, d_max=d_max, num_labels=L, jitter=0)
+    interior = [gy * 8 + gx for gy in range(1, 5) for gx in range(1, 7)]
+    st = H.fronto_state(o.S_total, d_true)
+    res = o.score(st, [(v, s, d_true, 0, 0, -1) for v in (0, 1) for s in interior])
+    assert max(r["tssd"] for r in res) < 1e-20
+    res2 = o.score(st, [(0, s, d_true * 1.05, 0, 0, -1) for s in interior])
+    assert min(r["tssd"] for r in res2) > 1e-6
+    sw = o.sweep([o.sp_base[v] + s for v in (0, 1) for s in interior], want_costs=True)
+    assert np.all(sw["label"] == k0)
+    planes = sw["planes"]
+    for v in (0, 1):
+        for s in interior:
+            assert np.isclose(planes[o.sp_base[v] + s, 0], d_true, rtol=1e-14)
+
+
+def test_tssd_symmetric_under_view_swap_with_integer_disparity():
+    rng = np.random.default_rng(8)
+    W, Hh, f, b, D = 40, 24, 60.0, 0.1, 3
+    d = f * b / D
+    K, R, t = H.parallel_rig([0.0, b], f, W, Hh)
+    img0, img1 = rng.uniform(size=(Hh, W, 3)), rng.uniform(size=(Hh, W, 3))
+    u = np.arange(W)[None, :].repeat(Hh, 0)
+    lab0 = (u >= D).astype(np.int32)          # pixels that land inside view 1
+    lab1 = (u > W - 1 - D).astype(np.int32)   # label 0: pixels that land inside view 0
+    o = make(K, R, t, [img0, img1], [lab0, lab1], 2, 1, T=10.0)
+    st = H.fronto_state(o.S_total, d)
+    r01, r10 = o.score(st, [(0, 1, d, 0, 0, -1), (1, 0, d, 0, 0, -1)])
+    assert r01["tssd"] > 1.0
+    assert abs(r01["tssd"] - r10["tssd"]) <= 1e-9 * r01["tssd"]
+    # the same sums computed from the images with the known pixel shift
+    ref = np.sum((img0[:, D:] - img1[:, :W - D]) ** 2)
+    assert np.isclose(r01["tssd"], ref, rtol=1e-9)
+
+
+def test_sweep_argmin_brute_force_and_jitter_wiring():
+    lf = synth.make_config(1, scale=0.25)
+    p = synth.method_params(lf, num_labels=16)
+    o = orc.Oracle(*synth.oracle_inputs(lf), p, threads=4)
+    items = np.arange(o.S_total)
+    sw = o.sweep(items, want_costs=True)
+    for it in range(o.S_total):
+        costs = sw["cost"][it]
+        k = int(np.argmin(costs))          # first minimum
+        assert sw["label"][it] == k
+        v = int(np.searchsorted(o.sp_base, it, side="right") - 1)
+        s = it - o.sp_base[v]
+        u = orc.jitter_u(p["seed"], 0, v, s, k)
+        z = 1 / p["d_max"] + (k + u) * o.delta
+        assert np.isclose(sw["planes"][it, 0], 1 / z, rtol=1e-15)
+        assert z >= 1 / p["d_max"] + k * o.delta and z < 1 / p["d_max"] + (k + 1) * o.delta
+
+
+# ---------------------------------------------------------------------------
+# smoothness term (Eq. 5-7)
+# ---------------------------------------------------------------------------
+
+def _two_view_grid(W=48, Hh=32, GW=6, GH=4, f=50.0, b=0.1, img0=None, img1=None, **pover):
+    K, R, t = H.parallel_rig([0.0, b], f, W, Hh)
+    lab = H.grid_label_map(W, Hh, GW, GH)
+    img0 = np.full((Hh, W, 3), 0.5) if img0 is None else img0
+    img1 = np.full((Hh, W, 3), 0.5) if img1 is None else img1
+    return make(K, R, t, [img0, img1], [lab, lab], GW, GH, **pover), lab, K
+
+
+def test_smoothness_one_for_a_common_slanted_plane():
+    o, lab, K = _two_view_grid()
+    n = np.array([0.3, -0.2, -1.0])
+    n /= np.linalg.norm(n)
+    rho = n @ np.array([0.0, 0.0, 2.5])                     # plane n.X = rho through (0,0,2.5)
+    Kinv = np.linalg.inv(K[0])
+    st = np.zeros((o.S_total, 4))
+    for v in (0, 1):
+        cen = o.sp_stats(v)["cen"]
+        for s in range(o.S[v]):
+            ray = Kinv @ [cen[s, 0], cen[s, 1], 1.0]
+            st[o.sp_base[v] + s] = [rho / (n @ ray), *n]    # depth along the ray (ray z = 1)
+    res = o.score(st, [(0, s, *st[s]) for s in (7, 8, 9, 14, 15, 16)])
+    for r in res:
+        assert abs(r["Es"] - 1.0) < 1e-12
+
+
+def test_smoothness_one_neighbour_off_by_sigma():
+    o, lab, K = _two_view_grid()
+    d = 2.5
+    st = H.fronto_state(o.S_total, d)
+    s, j = 8, 9                                             # (gx=2,gy=1) and its E neighbour
+    st[j, 0] = 1.0 / (1.0 / d + o.sigma)
+    r = o.score(st, [(0, s, d, 0, 0, -1)])[0]
+    assert abs(r["Es"] - (7 + math.exp(-0.5)) / 8) < 1e-12
+
+
+def test_smoothness_colour_weights():
+    alpha = 0.1
+    W, Hh, GW, GH = 48, 32, 6, 4
+    lab = H.grid_label_map(W, Hh, GW, GH)
+    C0 = np.array([0.5, 0.5, 0.5])
+    C1 = C0 + np.array([math.sqrt(2 * alpha ** 2 * math.log(2)), 0, 0])   # omega(C0, C1) = 1/2
+    s = 8
+    gx, gy = s % GW, s // GW
+    cols = np.tile(C0, (GW * GH, 1))
+    diag = [(gy + dy) * GW + gx + dx for dx, dy in [(1, -1), (-1, -1), (-1, 1), (1, 1)]]
+    cols[diag] = C1
+    img0 = H.colour_image_from_sp(lab, cols)
+    o, _, _ = _two_view_grid(img0=img0)
+    d = 2.5
+    st = H.fronto_state(o.S_total, d)
+    st[diag, 0] = 1.0 / (1.0 / d + o.sigma)
+    r = o.score(st, [(0, s, d, 0, 0, -1)])[0]
+    assert abs(r["Es"] - (4 + 2 * math.exp(-0.5)) / 6) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# consistency term (Eq. 8-11)
+# ---------------------------------------------------------------------------
+
+def _omega(a, b, alpha=0.1):
+    return math.exp(-np.sum((np.asarray(a) - np.asarray(b)) ** 2) / (2 * alpha ** 2))
+
+
+def test_visibility_closed_form_when_nearer_than_other_view():
+    W, Hh, GW, GH = 48, 32, 6, 4
+    lab = H.grid_label_map(W, Hh, GW, GH)
+    Cs, Cb, C1 = [0.7, 0.4, 0.3], [0.5, 0.5, 0.5], [0.62, 0.45, 0.3]
+    cols = np.tile(Cb, (GW * GH, 1))
+    s = 8
+    cols[s] = Cs
+    img0 = H.colour_image_from_sp(lab, cols)
+    img1 = np.tile(np.array(C1), (Hh, W, 1))
+    o, _, _ = _two_view_grid(img0=img0, img1=img1)
+    d0, d1 = 2.0, 2.2
+    st = H.fronto_state(o.S_total, d0)
+    st[o.sp_base[1]:] [:, 0] = d1                           # view 1 surface farther than the hypothesis
+    r = o.score(st, [(0, s, d0, 0, 0, -1)])[0]
+    G = math.exp(-(1 / d0 - 1 / d1) ** 2 / (2 * o.sigma ** 2))
+    assert r["nvalid"][0] == 64 and r["nx"][0] == 64 and r["ny"][0] == 0
+    assert abs(r["S"][0] - _omega(Cs, C1)) < 1e-12
+    assert abs(r["Vt"][0] - _omega(Cs, C1) * G) < 1e-12
+    assert r["O"][0] == 0.0
+    assert abs(r["Ec"] - _omega(Cs, C1) * G) < 1e-12
+    assert abs(r["E"] - r["Ec"] * r["Es"]) < 1e-15
+
+
+def test_occlusion_closed_form_when_behind_other_view():
+    W, Hh, GW, GH = 48, 32, 6, 4
+    lab = H.grid_label_map(W, Hh, GW, GH)
+    Cs, Cb, C1 = [0.7, 0.4, 0.3], [0.5, 0.5, 0.5], [0.62, 0.45, 0.3]
+    cols = np.tile(Cb, (GW * GH, 1))
+    s = 8
+    cols[s] = Cs
+    img0 = H.colour_image_from_sp(lab, cols)
+    img1 = np.tile(np.array(C1), (Hh, W, 1))
+    o, _, _ = _two_view_grid(img0=img0, img1=img1)
+    d0, d1 = 2.2, 2.0
+    st = H.fronto_state(o.S_total, d0)
+    st[o.sp_base[1]:, 0] = d1                               # view 1 surface nearer: P is occluded there
+    r = o.score(st, [(0, s, d0, 0, 0, -1)])[0]
+    minw = _omega(Cs, Cb)
+    assert r["nx"][0] == 0 and r["ny"][0] == 64
+    assert r["Vt"][0] == 0.0
+    assert abs(r["O"][0] - 0.5 * (1 - minw)) < 1e-12
+    assert abs(r["Ec"] - 0.5 * (1 - minw)) < 1e-12
+    # occlusion term switched off
+    o2, _, _ = _two_view_grid(img0=img0, img1=img1, term_mask=3)
+    r2 = o2.score(st, [(0, s, d0, 0, 0, -1)])[0]
+    assert r2["O"][0] == 0.0 and r2["E"] == 0.0
+
+
+def test_colour_similarity_uses_superpixel_hit_in_other_view():
+    # integer disparity 2 px: columns 16..23 of view 0 land on 14..21 of view 1,
+    # i.e. 2 columns in the superpixel gx=1 and 6 columns in gx=2 of view 1
+    W, Hh, GW, GH, f, b = 48, 32, 6, 4, 50.0, 0.1
+    d = f * b / 2.0
+    lab = H.grid_label_map(W, Hh, GW, GH)
+    Cs, CA, CB = [0.6, 0.5, 0.4], [0.55, 0.5, 0.4], [0.4, 0.6, 0.5]
+    cols0 = np.tile([0.5, 0.5, 0.5], (GW * GH, 1))
+    cols0[8] = Cs
+    cols1 = np.tile([0.5, 0.5, 0.5], (GW * GH, 1))
+    cols1[7] = CA
+    cols1[8] = CB
+    o, _, _ = _two_view_grid(img0=H.colour_image_from_sp(lab, cols0), img1=H.colour_image_from_sp(lab, cols1))
+    st = H.fronto_state(o.S_total, d)
+    r = o.score(st, [(0, 8, d, 0, 0, -1)])[0]
+    assert r["nvalid"][0] == 64
+    assert abs(r["S"][0] - (2 * _omega(Cs, CA) + 6 * _omega(Cs, CB)) / 8) < 1e-12
+
+
+def test_identity_view_gives_unit_consistency_and_zero_cost():
+    rng = np.random.default_rng(4)
+    W, Hh, GW, GH, f = 48, 32, 6, 4, 50.0
+    K, R, t = H.parallel_rig([0.0, 0.0], f, W, Hh)
+    lab = H.grid_label_map(W, Hh, GW, GH)
+    img = rng.uniform(size=(Hh, W, 3))
+    o = make(K, R, t, [img, img], [lab, lab], GW, GH, xy_eps=1e-9)
+    n = np.array([0.2, 0.1, -1.0])
+    n /= np.linalg.norm(n)
+    Kinv = np.linalg.inv(K[0])
+    st = np.zeros((o.S_total, 4))
+    rho = n @ np.array([0, 0, 2.0])
+    cen = o.sp_stats(0)["cen"]
+    for v in (0, 1):
+        for s in range(o.S[v]):
+            ray = Kinv @ [cen[s, 0], cen[s, 1], 1.0]
+            st[o.sp_base[v] + s] = [rho / (n @ ray), *n]
+    for s in (0, 8, 23):
+        r = o.score(st, [(0, s, *st[s])])[0]
+        # border pixels map onto the window edge itself: a flagged decision whose
+        # in-window outcome costs 0; interior superpixels are exactly 0
+        assert r["tssd_lo"] < 1e-20
+        if s == 8:
+            assert r["tssd"] < 1e-20 and r["flag_tssd"] == 0
+        assert abs(r["S"][0] - 1) < 1e-12 and abs(r["Vt"][0] - 1) < 1e-12 and r["O"][0] == 0
+        assert abs(r["E"] - 1) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# propagation and refinement (Section III-C, Eq. 4, Fig. 3) by brute force
+# ---------------------------------------------------------------------------
+
+def _tiny_scene():
+    # focal length, baselines and depths chosen so that no disparity is an exact
+    # integer or half-integer (no exact ties of nearest-pixel rounding)
+    W, Hh, f = 48, 32, 50.37
+    rig = synth.Rig(*H.parallel_rig([0.0, 0.1173, 0.2391], f, W, Hh), W, Hh)
+    rng = np.random.default_rng(21)
+    sc = synth.Scene()
+    sc.planes.append(synth._slanted_plane(rng, [0, 0, 4.13], 0.0, "y", 20, 20, 0.15, True, 3))
+    sc.planes.append(synth._slanted_plane(rng, [-0.3, 0.0, 2.0], 30.0, "y", 0.45, 0.5, 0.06, True, 9))
+    rgb, depth, obj = synth.render(rig, sc)
+    lab = H.grid_label_map(W, Hh, 6, 4)
+    return rig, rgb.numpy(), lab
+
+
+def _same_or_tie(a, b, sc_of):
+    """a equals b, or their admissible energy intervals overlap (a tie that
+    rounding may resolve either way)."""
+    if a == b:
+        return True
+    x, y = sc_of[a], sc_of[b]
+    return x["E_hi"] + 1e-12 >= y["E_lo"] and y["E_hi"] + 1e-12 >= x["E_lo"]
+
+
+def test_propagation_and_refinement_match_brute_force():
+    rig, rgb, lab = _tiny_scene()
+    p = H.params(num_labels=24, kernel_size_init=32, kernel_step_sp=1.0)
+    o = orc.Oracle(rig.K, rig.R, rig.t, list(rgb), [lab] * 3, 6, 4, p, threads=4)
+    planes = o.sweep()["planes"]
+    Kinv = np.linalg.inv(rig.K[0])
+    size_init, steps_init = o.kernel_params(0)
+    for it in (1, 2):
+        res = o.iterate(it, planes, cand_cap=256)
+        offs = orc.kernel_offsets(size_init, steps_init, it)
+        for v in range(3):
+            cen = o.sp_stats(v)["cen"]
+            for s in range(o.S[v]):
+                gs = o.sp_base[v] + s
+                gx, gy = s % 6, s // 6
+                cu = np.array([cen[s, 0], cen[s, 1], 1.0])
+                ray = Kinv @ cu
+                # enumerate the kernel's candidate planes, re-anchored at the own centroid
+                cands = [(0, planes[gs])]
+                for m in range(1, len(offs)):
+                    x, y = gx + offs[m][0], gy + offs[m][1]
+                    if not (0 <= x < 6 and 0 <= y < 4):
+                        continue
+                    j = y * 6 + x
+                    dj, nj = planes[o.sp_base[v] + j, 0], planes[o.sp_base[v] + j, 1:]
+                    Pj = dj * (Kinv @ [cen[j, 0], cen[j, 1], 1.0])
+                    dhat = (nj @ Pj) / (nj @ ray)              # ray-plane intersection depth
+                    if not (p["d_min"] <= dhat <= p["d_max"]):
+                        continue
+                    if abs(nj @ ray) / np.linalg.norm(ray) < 0.1:
+                        continue
+                    cands.append((m, np.array([dhat, *nj])))
+                scores = o.score(planes, [(v, s, *c[1]) for c in cands])
+                sc_of = {m: sc for (m, _), sc in zip(cands, scores)}
+                best, bestE = 0, scores[0]["E"]
+                for (m, _), sc in zip(cands, scores):
+                    if sc["E"] > bestE:
+                        best, bestE = m, sc["E"]
+                it_i = gs
+                m_o = int(res["choice"][it_i, 0])
+                assert m_o in sc_of and _same_or_tie(m_o, best, sc_of)
+                assert sc_of[m_o]["E_lo"] - 1e-12 <= res["energy"][it_i, 0] <= sc_of[m_o]["E_hi"] + 1e-12
+                # refinement: normals of the ring triangles (Fig. 3b), from the
+                # oracle's post-propagation depth
+                dnew = dict(cands)[m_o][0]
+                P0 = dnew * ray
+                pts = []
+                for (dx, dy) in RING:
+                    x, y = gx + dx, gy + dy
+                    if 0 <= x < 6 and 0 <= y < 4:
+                        j = y * 6 + x
+                        pts.append(planes[o.sp_base[v] + j, 0] * (Kinv @ [cen[j, 0], cen[j, 1], 1.0]))
+                    else:
+                        pts.append(None)
+                tri = []
+                for tI in range(8):
+                    a, b = pts[tI], pts[(tI + 1) % 8]
+                    if a is None or b is None:
+                        continue
+                    nrm = np.cross(a - P0, b - P0)
+                    nrm /= np.linalg.norm(nrm)
+                    if nrm @ P0 > 0:
+                        nrm = -nrm
+                    if abs(nrm @ ray) / np.linalg.norm(ray) < 0.1:
+                        continue
+                    tri.append((tI, np.array([dnew, *nrm])))
+                tsc = o.score(planes, [(v, s, *c[1]) for c in tri]) if tri else []
+                rsc_of = {-1: sc_of[m_o]}
+                rbest, rE = -1, sc_of[m_o]["E"]
+                for (tI, _), sc in zip(tri, tsc):
+                    rsc_of[tI] = sc
+                    if sc["E"] > rE:
+                        rbest, rE = tI, sc["E"]
+                t_o = int(res["choice"][it_i, 1])
+                assert t_o in rsc_of and _same_or_tie(t_o, rbest, rsc_of)
+                assert rsc_of[t_o]["E_lo"] - 1e-12 <= res["energy"][it_i, 1] <= rsc_of[t_o]["E_hi"] + 1e-12
+                want = dict(tri)[t_o] if t_o >= 0 else dict(cands)[m_o]
+                assert np.allclose(res["planes"][gs], want, rtol=1e-12, atol=1e-12)
+        planes = res["planes"]
+
+
+# ---------------------------------------------------------------------------
+# invariants
+# ---------------------------------------------------------------------------
+
+def test_jacobi_result_independent_of_order_and_threads_and_never_worse():
+    lf = synth.make_config(1, scale=0.5)
+    p = synth.method_params(lf, num_labels=24)
+    args = synth.oracle_inputs(lf)
+    o1 = orc.Oracle(*args, p, threads=1)
+    o8 = orc.Oracle(*args, p, threads=8)
+    planes = o1.sweep()["planes"]
+    assert np.array_equal(planes, o8.sweep()["planes"])
+    r1 = o1.iterate(1, planes)
+    perm = np.random.default_rng(0).permutation(o8.S_total).astype(np.int32)
+    r8 = o8.iterate(1, planes, items=perm)
+    assert np.array_equal(r1["planes"], r8["planes"])
+    assert np.array_equal(r1["choice"][perm], r8["choice"])
+    # the chosen plane's energy is never below the current plane's (Section III-C)
+    cur = o1.score(planes, [(v, s, *planes[o1.sp_base[v] + s]) for v in range(3) for s in range(o1.S[v])])
+    cur_E = np.array([c["E"] for c in cur])
+    assert np.all(r1["energy"][:, 1] >= cur_E - 1e-15)
+    assert np.all(r1["energy"][:, 1] >= r1["energy"][:, 0])
+
+
+def test_recovery_on_rendered_planes_improves_with_iterations():
+    lf = synth.make_config(1)
+    p = synth.method_params(lf)
+    o = orc.Oracle(*synth.oracle_inputs(lf, synth.rgba8_as_float(synth.quantize_rgba8(lf.rgb))), p)
+    gt = synth.gt_planes(lf).reshape(-1, 4)
+    planes, hist = o.run()
+    m = gt[:, 0] > 0
+
+    def med(pl):
+        return float(np.median(np.abs(1 / pl[m, 0] - 1 / gt[m, 0]) * gt[m, 0]))
+
+    errs = [med(h) for h in hist]
+    assert errs[-1] < errs[0]
+    assert errs[-1] < 0.01          # median relative inverse-depth error below 1 %
