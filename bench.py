@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the superpixel plane-sweep + propagation hot path on GB300.
+
+One step = one whole frame through lfd_estimate: superpixel build, plane
+sweep, every refinement iteration and the final depth rasterisation, on a
+synthetic camera-array scene shaped like the paper's workloads.  The headline
+metric is plane-hypothesis evaluations per second (a (superpixel, candidate
+plane) scoring over all its pixels and neighbour views); ms per view and
+pixel-view samples per second are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 2] [--impl ours|reference]
+
+N > 1 runs under torch.distributed.run: independent replicas (the hot path has
+no exchange step at one light field per GPU), value = all ranks' evaluations
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "plane-hypothesis evals/s"
+UNIT = "evals/s"
+L2_FLUSH_BYTES = 256 << 20
+# algorithmic FP32 operations per pixel-view sample (counted from the method's
+# arithmetic, address arithmetic excluded)
+FLOPS_PER_SAMPLE = {"sweep": 48, "propagate": 34}
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload_name(cfg: int, lf) -> str:
+    V, W, H = lf.rig.V, lf.rig.W, lf.rig.H
+    S = lf.GW * lf.GH
+    p = lf.params
+    fmt = "FP16" if cfg == 3 else "RGBA8"
+    return (f"config {cfg} ({lf.name}): {V} views {W}x{H} {fmt}, {S} superpixels/view, "
+            f"{p['num_labels']} labels, {p['iterations']} iterations")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def build_inputs(cfg: int, device: str):
+    from paper_1812_06856_gb300 import synth
+    lf = synth.make_config(cfg, device=device)
+    if cfg == 3:
+        views = synth.to_rgba_float(lf.rgb, torch.float16).to(device)
+    else:
+        views = synth.quantize_rgba8(lf.rgb).to(device)
+    labels = torch.from_numpy(np.ascontiguousarray(lf.labels)).to(device)
+    params = synth.method_params(lf)
+    return lf, views, labels, params
+
+
+def cpu_oracle_rate(lf, views, params, planes_gpu, sample_frac: float, seconds_hint: float = 15.0, threads=None):
+    """Oracle (FP64 CPU reference) throughput on a deterministic superpixel sample:
+    the sweep of the sample and one refinement iteration (iteration 1, the widest
+    kernel) of the sample from the GPU's sweep state.  Returns (evals/s, info)."""
+    from oracle import oracle as orc
+    from paper_1812_06856_gb300 import synth
+    if views.dtype == torch.uint8:
+        rgb = synth.rgba8_as_float(views.cpu())
+    else:
+        rgb = views[..., :3].to(torch.float64).cpu()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = threads or cores
+    o = orc.Oracle(*synth.oracle_inputs(lf, rgb), params, threads=threads)
+    rng = np.random.default_rng(1234)
+    n = max(threads, int(round(sample_frac * o.S_total)))
+    items = np.sort(rng.choice(o.S_total, size=min(n, o.S_total), replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    sw = o.sweep(items)
+    t1 = time.perf_counter()
+    res = o.iterate(1, planes_gpu, items=items, cand_cap=2048)
+    t2 = time.perf_counter()
+    ne = sw["label"] >= 0
+    hyp = int(ne.sum()) * int(params["num_labels"])
+    hyp += int(np.isfinite(res["cand"][:, :, 0]).sum() + np.isfinite(res["ref"][:, :, 0]).sum())
+    info = {"superpixels": int(len(items)), "of": int(o.S_total), "sweep_s": t1 - t0, "iterate_s": t2 - t1,
+            "hypotheses": hyp, "threads": threads, "cores": cores}
+    return hyp / (t2 - t0), info
+
+
+def run_reference(args):
+    """--impl reference: the oracle as it stands on the host cores, on a bounded
+    superpixel sample of the same workload per step."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_1812_06856_gb300 import synth
+    orc.build()
+    lf = synth.make_config(args.config, device="cpu")
+    if args.config == 3:
+        views = synth.to_rgba_float(lf.rgb, torch.float16)
+    else:
+        views = synth.quantize_rgba8(lf.rgb)
+    params = synth.method_params(lf)
+    rgb = synth.rgba8_as_float(views) if views.dtype == torch.uint8 else views[..., :3].to(torch.float64)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    o = orc.Oracle(*synth.oracle_inputs(lf, rgb), params, threads=cores)
+    frac = args.ref_sample
+    rng = np.random.default_rng(99)
+    n = max(cores, int(round(frac * o.S_total)))
+    planes0 = np.zeros((o.S_total, 4))
+    times, hyps = [], []
+    for step in range(args.warmup + args.steps):
+        items = np.sort(rng.choice(o.S_total, size=n, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        sw = o.sweep(items)
+        state = sw["planes"] if step == 0 else planes0
+        planes0 = state
+        res = o.iterate(1, state, items=items, cand_cap=2048)
+        dt = time.perf_counter() - t0
+        h = int((sw["label"] >= 0).sum()) * int(params["num_labels"])
+        h += int(np.isfinite(res["cand"][:, :, 0]).sum() + np.isfinite(res["ref"][:, :, 0]).sum())
+        if step >= args.warmup:
+            times.append(dt)
+            hyps.append(h)
+    value = sum(hyps) / sum(times)
+    sample = (f"{n} of {o.S_total} superpixels per step (deterministic random sample): their sweep and "
+              f"refinement iteration 1; FP64 oracle, {cores} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.config, lf), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    from paper_1812_06856_gb300 import lfd
+    lf, views, labels, params = build_inputs(args.config, dev)
+    V, H, W = lf.rig.V, lf.rig.H, lf.rig.W
+    ctx = lfd.Context(local)
+    K, R, t, GW, GH = lf.rig.K, lf.rig.R, lf.rig.t, lf.GW, lf.GH
+    S_total = V * GW * GH
+    planes = torch.zeros((S_total, 4), dtype=torch.float32, device=dev)
+    depth = torch.zeros((V, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.estimate(views, labels, K, R, t, GW, GH, params, out_planes=planes, out_depth=depth)
+
+    for _ in range(max(args.warmup, 1)):
+        flush.fill_(1)
+        step()
+    ctx.synchronize()
+    hyp_step, samples_step = ctx.counters()
+    ctx.profile_read()                                   # reset stage timers / launch counts
+    ctx.profile_enable(True)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    w0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)                            # L2 flush outside the timed events
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - w0
+    clock_info = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ctx.synchronize()
+    ms = float(np.mean(step_ms))
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = hyp_step * ws / (ms / 1000.0)
+
+    # dominant kernel and its roofline
+    stage_ms = {k: v[0] / args.steps for k, v in prof.items()}
+    stage_launches = {k: v[1] / args.steps for k, v in prof.items()}
+    sweep_samples = int(params["num_labels"]) * V * H * W * min(V - 1, 8)
+    prop_samples = samples_step - sweep_samples
+    dom = max(("sweep", "propagate"), key=lambda k: stage_ms[k])
+    dom_samples = sweep_samples if dom == "sweep" else prop_samples
+    launches = max(stage_launches[dom], 1)
+    avg_launch_ms = stage_ms[dom] / launches
+    flops_per_launch = FLOPS_PER_SAMPLE[dom] * dom_samples / launches
+    achieved = flops_per_launch / (avg_launch_ms / 1000.0) / 1e12
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_note": f"FP32 FMA peak {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                             f"{sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
+                "algorithmic": f"{FLOPS_PER_SAMPLE[dom]} FP32 flop per pixel-view sample x "
+                               f"{dom_samples / launches:.4g} samples per launch",
+                "avg_launch_ms": avg_launch_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args.config, lf), "l2": "flushed between steps (256 MiB write)",
+                       "inputs": "device-resident", "parallelism": f"replicas x{ws}"},
+            "ms_per_view": ms / V, "samples_per_s": samples_step * ws / (ms / 1000.0),
+            "hypotheses_per_step": hyp_step, "samples_per_step": samples_step,
+            "stage_ms": stage_ms, "wall_s": wall,
+            "gpu_launches": int(sum(v[1] for v in prof.values())),
+            "roofline": roofline, "clocks": clock_info}
+
+    # end to end through the host-memory entry point
+    if not args.no_e2e:
+        vh = views.cpu().pin_memory()
+        lh = labels.cpu().pin_memory()
+        ph = torch.zeros((S_total, 4), dtype=torch.float32).pin_memory()
+        dh = torch.zeros((V, H, W), dtype=torch.float32).pin_memory()
+        ctx_h = lfd.Context(local)
+        for _ in range(max(args.warmup, 1)):
+            ctx_h.estimate_host(vh, lh, K, R, t, GW, GH, params, ph, dh)
+        ctx_h.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            evs[k][0].record(stream)
+            ctx_h.estimate_host(vh, lh, K, R, t, GW, GH, params, ph, dh)
+            evs[k][1].record(stream)
+        barrier()
+        e_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        if ws > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        line["e2e"] = {"value": hyp_step * ws / (e_ms / 1000.0), "unit": UNIT,
+                       "h2d_bytes_per_step": int(vh.numel() * vh.element_size() + lh.numel() * 4),
+                       "d2h_bytes_per_step": int(ph.numel() * 4 + dh.numel() * 4), "ms_per_step": e_ms}
+        ctx_h.close()
+
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, info = cpu_oracle_rate(lf, views, params, planes_sweep_state(ctx, lf, views, labels, params),
+                                     args.cpu_sample)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
+                                "sample": f"{info['superpixels']} of {info['of']} superpixels (deterministic random "
+                                          f"sample): their sweep ({info['sweep_s']:.1f} s) and refinement "
+                                          f"iteration 1 ({info['iterate_s']:.1f} s) from the GPU sweep state, "
+                                          f"{info['hypotheses']} hypotheses"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def planes_sweep_state(ctx, lf, views, labels, params):
+    ctx.set_input(views, labels, lf.rig.K, lf.rig.R, lf.rig.t, lf.GW, lf.GH, params)
+    planes, _, _ = ctx.plane_sweep()
+    ctx.synchronize()
+    return planes.cpu().numpy().astype(np.float64)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=float, default=0.01, help="superpixel fraction timed on the CPU oracle")
+    ap.add_argument("--ref-sample", type=float, default=0.004, help="superpixel fraction per reference step")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("note: timing rules ask for at least 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

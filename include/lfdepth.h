@@ -1,0 +1,293 @@
+/*
+ * lfdepth — superpixel light-field depth estimation on one NVIDIA GB300
+ * (sm_103a): the data-parallel hot path of Chuchvara, Barsi, Gotchev,
+ * "Fast and Accurate Depth Estimation from Sparse Light Fields"
+ * (arXiv 1812.06856), Section III-B (plane sweep), III-C (propagation and
+ * plane refinement with the energy of Eq. 3-11) and III-E (all superpixels of
+ * all views in parallel, ping-pong plane buffers).
+ *
+ * Conventions used by every call
+ *  - Cameras: a world point X maps to camera coordinates x = R X + t; the
+ *    pixel is K x / x_z, pixel centres at integer coordinates (0..W-1,
+ *    0..H-1), x right, y down, z forward.  K must be pinhole (last row 0 0 1).
+ *  - Colours are RGB in [0,1]: RGBA8 texels are value/255; the alpha channel
+ *    is ignored.
+ *  - Superpixels: label maps are row-major int32 H x W per view with values in
+ *    [0, grid_w * grid_h); label = gy * grid_w + gx places the superpixel on a
+ *    regular grid whose 8-neighbourhood is the paper's neighbour system
+ *    (Section III-A).  Empty labels are allowed.
+ *  - Planes: one float4 {d, nx, ny, nz} per superpixel, in the camera frame of
+ *    its view: d > 0 is the depth (camera z) at the superpixel centroid and n
+ *    the unit normal facing the camera (Section II, III-A: "a single depth value
+ *    at a superpixel centroid and a normal vector").  {0,0,0,0} marks an
+ *    empty superpixel / no plane.
+ *  - Depth maps: float32 H x W per view, camera z of the pixel's superpixel
+ *    plane along the pixel ray, 0 where there is none.
+ *  - Streams: every call that takes `stream` (a cudaStream_t, NULL = legacy
+ *    default stream) only enqueues work on it and returns; inputs must stay
+ *    alive and outputs untouched until the stream has passed the call.
+ *    Calls documented as synchronous wait for their own work.
+ *  - Errors: every call returns an lfd_status and never throws; after a
+ *    failure lfd_last_error(ctx) describes it.  Invalid arguments are
+ *    reported before anything is enqueued.  Device-side checks (labels out of
+ *    range) raise a status word that the next lfd_synchronize() reports as
+ *    LFD_ERR_DEVICE_CHECK.
+ *  - Ownership: the caller owns every buffer it passes; the context owns its
+ *    workspace (superpixel lists and statistics, sampling textures, rasterised
+ *    maps, ping-pong planes) and frees it in lfd_destroy().
+ *  - One context serves one light field at a time and is not thread safe;
+ *    use one context per concurrent light field.
+ */
+#ifndef LFDEPTH_H
+#define LFDEPTH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LFD_VERSION 1
+#define LFD_MAX_NEIGHBOR_VIEWS 8   /* |N(v)| of Eq. 2 / Eq. 8 is at most this */
+#define LFD_MAX_VIEWS 256
+#define LFD_MAX_LABELS 4096
+#define LFD_MAX_ITER_INDEX 64      /* iteration index I of Eq. 4 (plus warm offset) */
+#define LFD_MAX_DIM 32767          /* image width / height */
+/* per-query record of lfd_score(): LFD_TERMS_HEAD scalars then, for each
+ * neighbour view k < LFD_MAX_NEIGHBOR_VIEWS, LFD_TERMS_PER_VIEW scalars */
+#define LFD_TERMS_HEAD 4           /* E, E_s, E_c, TSSD sum */
+#define LFD_TERMS_PER_VIEW 6       /* S_i, V_i, O_i, |Omega_i|, |X_i|, |Y_i| */
+#define LFD_TERMS_STRIDE (LFD_TERMS_HEAD + LFD_MAX_NEIGHBOR_VIEWS * LFD_TERMS_PER_VIEW)
+
+typedef int32_t lfd_status;
+enum {
+    LFD_OK = 0,
+    LFD_ERR_INVALID_ARG = 1,   /* a documented precondition does not hold */
+    LFD_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    LFD_ERR_OOM = 3,           /* device or pinned memory allocation failed */
+    LFD_ERR_BUDGET = 4,        /* the workspace would exceed the context's HBM budget */
+    LFD_ERR_TIMEOUT = 5,       /* a bounded wait ran out */
+    LFD_ERR_DEVICE_CHECK = 6,  /* a device-side input check failed (see lfd_last_error) */
+    LFD_ERR_BUSY = 7,
+    LFD_ERR_STATE = 8          /* call order: e.g. lfd_iterate before lfd_set_input */
+};
+
+typedef enum {
+    LFD_RGBA8 = 0,      /* 4 x uint8 per texel */
+    LFD_RGBA_F16 = 1,   /* 4 x IEEE half per texel */
+    LFD_RGBA_BF16 = 2,  /* 4 x bfloat16 per texel */
+    LFD_RGBA_F32 = 3    /* 4 x float per texel */
+} lfd_pixfmt;
+
+typedef struct {
+    double K[9];        /* row-major intrinsics, last row 0 0 1 */
+    double R[9];        /* row-major world -> camera rotation */
+    double t[3];        /* world -> camera translation */
+    int32_t width, height;
+} lfd_camera;
+
+typedef struct {
+    int32_t num_views;                   /* V >= 2 */
+    int32_t fmt;                         /* lfd_pixfmt of every view */
+    const lfd_camera *cams;              /* host array [V] */
+    const void *const *views;            /* host array [V] of image pointers (device memory, or host
+                                            memory for lfd_estimate_host), H rows of pitch bytes */
+    const int64_t *view_pitch_bytes;     /* host array [V]; NULL or 0 entries = width * texel size */
+    const int32_t *const *labels;        /* host array [V] of label-map pointers, tightly packed H x W */
+    const int32_t *grid_w;               /* host array [V] */
+    const int32_t *grid_h;               /* host array [V] */
+} lfd_lightfield;
+
+/* Parameters.  lfd_params_default() fills the values in brackets. */
+typedef struct {
+    double d_min, d_max;         /* scene depth range, 0 < d_min < d_max (Section III-B) */
+    int32_t num_labels;          /* L inverse-depth levels of the sweep [64], 1..LFD_MAX_LABELS */
+    int32_t iterations;          /* refinement iterations [5] (Section IV-A) */
+    double T;                    /* truncation of Eq. 1 on RGB in [0,1] [0.04] */
+    double sigma;                /* Eq. 6 / Eq. 10 Gaussian width; 0 = 2 x bin width of the domain [0] */
+    double alpha;                /* Eq. 7 colour width [0.1] */
+    double eta;                  /* Eq. 11 occlusion regulariser [0.5] */
+    int32_t kernel_size_init;    /* initial kernel size in pixels, 0 = smallest image dimension
+                                    (Section IV-A) [0] */
+    double kernel_step_sp;       /* kernel step in superpixels (Section IV-A) [5] */
+    int32_t max_neighbor_views;  /* |N(v)|: nearest camera centres, 1..8, 0 = 8 [0] */
+    int32_t depth_domain;        /* Gaussians of Eq. 6/10 and the X/Y split: 0 inverse depth, 1 depth [0] */
+    int32_t jitter;              /* 1: one uniform sample per inverse-depth bin (Section III-B);
+                                    0: bin centres [1] */
+    uint32_t term_mask;          /* bit0 smoothness E_s, bit1 consistency E_c, bit2 occlusion O [7] */
+    int32_t sweep_frame;         /* sweep planes fronto-parallel to 0 the view's camera, 1 the world [0] */
+    uint64_t seed;               /* jitter seed [0x5EED] */
+    int32_t lf_index;            /* light-field index mixed into the jitter key [0] */
+    double xy_eps;               /* relative tolerance of the X/Y split of Eq. 10/11 [0] */
+    int32_t warm_iter_offset;    /* iteration I of Eq. 4 is iter + offset (warm starts) [0] */
+} lfd_params;
+
+/* one hypothesis for lfd_score(): plane {d, n} of superpixel `sp` of `view` */
+typedef struct {
+    int32_t view, sp;
+    float d, nx, ny, nz;
+} lfd_query;
+
+typedef struct lfd_ctx lfd_ctx;
+
+/* ---- library ---------------------------------------------------------- */
+
+int32_t lfd_version(void);
+/* ABI check for bindings: writes sizeof(lfd_camera), sizeof(lfd_lightfield),
+ * sizeof(lfd_params), sizeof(lfd_query) into out[0..3]. */
+void lfd_struct_sizes(int32_t *out);
+const char *lfd_status_string(lfd_status s);
+void lfd_params_default(lfd_params *p);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * workspace the context may allocate (0 = no bound).  *out receives the
+ * context; allocation is deferred to lfd_set_input. */
+lfd_status lfd_create(lfd_ctx **out, int32_t device, uint64_t hbm_budget_bytes);
+/* Free the context and its workspace (waits for its work first). */
+lfd_status lfd_destroy(lfd_ctx *ctx);
+/* Message of the last failure on ctx (never NULL; "" after success). */
+const char *lfd_last_error(const lfd_ctx *ctx);
+
+/* ---- staged hot path -------------------------------------------------- */
+
+/* Bind a light field and parameters to the context: validate them, size the
+ * workspace (LFD_ERR_BUDGET past the budget), copy the cameras, choose each
+ * view's neighbour views N(v) (the min(V-1, max_neighbor_views) nearest camera
+ * centres, nearer first, ties to the lower index), build each view's sampling
+ * texture from `views`, and build the superpixels (Section III-A; step a1):
+ * per label the row-major pixel list, the centroid, the mean colour C_Omega
+ * and the minimum colour similarity to the present 8-neighbours (Eq. 11).
+ * Views and labels are device pointers and are read only during this call's
+ * stream work.  Asynchronous. */
+lfd_status lfd_set_input(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_params *p, void *stream);
+
+/* Number of superpixels (grid_w * grid_h) of `view` of the bound light field. */
+lfd_status lfd_num_superpixels(const lfd_ctx *ctx, int32_t view, int32_t *out);
+
+/* Plane sweep (Section III-B, Eq. 1-2; steps a2-a4): for every superpixel of
+ * every view, L fronto-parallel planes at inverse depths
+ * 1/d_max + (k + u_k) (1/d_min - 1/d_max) / L, u_k uniform in [0,1) per
+ * superpixel and label (SplitMix64 of seed ^ key, key = ((lf*2^12 + v)*2^20 +
+ * s)*2^12 + k), are scored by the sum over N(v) and the superpixel's pixels
+ * of min(T, SSD) with bilinear sampling through the plane-induced homography
+ * (a projection outside view i or behind a camera costs T); the lowest cost
+ * wins (lowest k on ties).
+ *   planes_out: host array [V] of device float4[S_v] (required).
+ *   label_out:  host array [V] of device int32[S_v] winning k, -1 if empty (nullable).
+ *   cost_out:   host array [V] of device float[S_v * L], all costs (nullable).
+ * Asynchronous. */
+lfd_status lfd_plane_sweep(lfd_ctx *ctx, float *const *planes_out, int32_t *const *label_out,
+                           float *const *cost_out, void *stream);
+
+/* Depth rasteriser (step a5): every pixel's depth from its superpixel's plane
+ * (the plane's camera z along the pixel ray; 0 if the plane is behind the
+ * camera or missing), into the context's sampling maps used by lfd_iterate's
+ * visibility test of Eq. 10, and into depth_out if given.
+ *   planes: host array [V] of device float4[S_v].
+ *   depth_out: host array [V] of device float[H*W] (nullable).
+ * Asynchronous. */
+lfd_status lfd_rasterize(lfd_ctx *ctx, const float *const *planes, float *const *depth_out, void *stream);
+
+/* One refinement iteration (Section III-C, III-E; steps a5-a7): rasterise
+ * planes_in, then for every superpixel of every view, in parallel and reading
+ * only planes_in (Jacobi): propagation — the current plane and the planes of
+ * the kernel's superpixels (the 8 neighbours, then along 8 compass rays the
+ * cells at r_k = max(1, floor(k Size_I/Steps_I + 0.5)), k = 1..Steps_I, with
+ * Size_I = Size_init/I, Steps_I = max(1, floor(Steps_init/I)) (Eq. 4)), each
+ * re-anchored at the own centroid and rejected if its depth there leaves
+ * [d_min, d_max] or it is grazing (|n . ray| < 0.1), replace the current plane
+ * when E = E_c E_s (Eq. 3) is strictly greater; refinement — the normals of the
+ * 8 ring triangles (own centroid at the new depth and two consecutive
+ * neighbour centroids at their depths; Fig. 3b) replace the normal on strict
+ * improvement.  iter is the 1-based I of Eq. 4 (warm_iter_offset is added).
+ *   planes_in / planes_out: host arrays [V] of device float4[S_v]; must not alias.
+ *   choice_out: host array [V] of device int32[2*S_v]: propagation candidate index
+ *               (0 = current), refinement triangle (-1 = none) (nullable).
+ *   energy_out: host array [V] of device float[2*S_v]: E after propagation and after
+ *               refinement (nullable).
+ * Asynchronous. */
+lfd_status lfd_iterate(lfd_ctx *ctx, int32_t iter, const float *const *planes_in, float *const *planes_out,
+                       int32_t *const *choice_out, float *const *energy_out, void *stream);
+
+/* Whole frame (steps a1-a8): lfd_set_input, then the plane sweep (or
+ * warm_planes when given), then p->iterations iterations ping-ponging two
+ * workspace buffers, then the final planes into planes_out and their depth
+ * maps into depth_out (nullable).  All pointers in lf and the outputs are
+ * device pointers; warm_planes is a host array [V] of device float4[S_v] or
+ * NULL.  Asynchronous. */
+lfd_status lfd_estimate(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_params *p,
+                        const float *const *warm_planes, float *const *planes_out, float *const *depth_out,
+                        void *stream);
+
+/* lfd_estimate with every image, label map and output in HOST memory: the
+ * call copies the inputs to the device, runs the frame and copies the planes
+ * and depth maps back.  Pinned host memory makes the copies asynchronous;
+ * the call returns after enqueueing and the results are valid once the
+ * stream has passed it (lfd_synchronize). */
+lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const lfd_params *p,
+                             float *const *planes_out_host, float *const *depth_out_host, void *stream);
+
+/* Wait for the stream and report device-side check failures
+ * (LFD_ERR_DEVICE_CHECK) raised by this context's kernels; clears them. */
+lfd_status lfd_synchronize(lfd_ctx *ctx, void *stream);
+
+/* Hypotheses scored and pixel-view samples taken by this context's kernels
+ * since the last lfd_set_input / lfd_estimate (synchronous). */
+lfd_status lfd_counters(lfd_ctx *ctx, uint64_t *hypotheses, uint64_t *samples, void *stream);
+
+/* ---- tracing ------------------------------------------------------------ */
+
+/* Stages timed by the tracer. */
+enum {
+    LFD_STAGE_SUPERPIXELS = 0,  /* step a1 kernels of lfd_set_input */
+    LFD_STAGE_SWEEP = 1,        /* steps a2-a4 */
+    LFD_STAGE_RASTER = 2,       /* step a5 (plane coefficients + rasteriser) */
+    LFD_STAGE_PROPAGATE = 3,    /* steps a6-a7 */
+    LFD_STAGES = 4
+};
+
+/* Enable (1) or disable (0) CUDA-event timing of every kernel launch of the
+ * context, recorded on the launching stream around each launch.  Launch
+ * counts are kept whether or not timing is enabled. */
+lfd_status lfd_profile_enable(lfd_ctx *ctx, int32_t enable);
+/* Synchronous: wait for the recorded events, then write per stage the summed
+ * kernel time in milliseconds (ms_out[LFD_STAGES], nullable) and the number
+ * of launches (launches_out[LFD_STAGES], nullable) since the last read, and
+ * reset both. */
+lfd_status lfd_profile_read(lfd_ctx *ctx, double *ms_out, int64_t *launches_out);
+
+/* ---- inspection (tests, tools; synchronous) ---------------------------- */
+
+/* Per-hypothesis terms (Eq. 1-11) of nq planes under the state
+ * `state_planes` (host array [V] of device float4[S_v], rasterised first):
+ * out (host, nq * LFD_TERMS_STRIDE floats) receives per query
+ * E, E_s, E_c, the TSSD sum of Eq. 2, then for each neighbour view k:
+ * S_k (Eq. 9), V_k (Eq. 10), O_k (Eq. 11), |Omega_k|, |X_k|, |Y_k|.
+ * queries: host array [nq]. */
+lfd_status lfd_score(lfd_ctx *ctx, const float *const *state_planes, int32_t nq, const lfd_query *queries,
+                     float *out, void *stream);
+
+/* Superpixel lists and statistics of `view` (host outputs, any may be NULL):
+ * offsets int32[S+1], pixels int32[H*W] (row-major linear index, row-major
+ * order inside each superpixel), stats float[S*8] = {cx, cy, r, g, b, minw,
+ * count, 0}; neighbours int32[LFD_MAX_NEIGHBOR_VIEWS] of N(view) (-1 padded). */
+lfd_status lfd_get_superpixels(lfd_ctx *ctx, int32_t view, int32_t *offsets, int32_t *pixels, float *stats,
+                               int32_t *neighbours, void *stream);
+
+/* ---- host logic (no GPU needed) ---------------------------------------- */
+
+/* N(v) for every view: out[v * LFD_MAX_NEIGHBOR_VIEWS + k], -1 padded;
+ * *k_out = min(V-1, max_k or 8). */
+lfd_status lfd_neighbor_views(const lfd_camera *cams, int32_t V, int32_t max_k, int32_t *out, int32_t *k_out);
+
+/* Kernel offsets of iteration I (Eq. 4, Fig. 3a): (0,0), the 8 neighbours
+ * E NE N NW W SW S SE, then ray cells by k (see lfd_iterate) without repeats,
+ * as dx,dy pairs into dxdy[2*cap]; returns the count (writes nothing when it
+ * exceeds cap).  size_init / steps_init in superpixel cells. */
+int32_t lfd_kernel_offsets(int32_t size_init, int32_t steps_init, int32_t I, int32_t *dxdy, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LFDEPTH_H */

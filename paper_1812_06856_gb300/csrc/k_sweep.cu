@@ -1,0 +1,217 @@
+// Steps a2-a4: partly randomised fronto-parallel plane sweep (Section III-B).
+//
+// For superpixel Omega of view v and label k the plane is fronto-parallel at
+// inverse depth z_k = 1/d_max + (k + u_k) * delta with u_k uniform in [0,1)
+// per superpixel and label (the jitter of Section III-B).  Its cost is
+// Eq. 2's double sum over the neighbour views N(v) and the superpixel's
+// pixels of the truncated SSD of Eq. 1, sampled bilinearly through the
+// plane-induced homography; the lowest cost wins.
+//
+// Mapping: one CTA per superpixel, one thread per label.  The superpixel's
+// pixels are staged in shared memory and read as broadcasts, so every thread
+// walks the same pixel list while its own label shifts the projection along
+// the epipolar line; neighbouring labels therefore gather from neighbouring
+// texels (coalesced, L1-resident).  No reduction is needed per sample: each
+// thread owns its label's cost; a single block arg-min ends the CTA.
+//
+// Homography per (label, view): for the plane g = z_k * gh (gh = (0,0,1) for
+// camera-frame sweeps) A = P + q g^T; its superpixel-anchored third column
+// (P + q g^T) (ref,1) is composed in FP64 and rounded to FP32; per sample the
+// projection is 6 FP32 FMAs on offsets from the anchor.
+#include "lfd_sample.cuh"
+
+namespace lfd {
+
+constexpr int SWEEP_THREADS = 256;
+constexpr int SWEEP_CHUNK = 128;
+
+struct SweepPair {
+    float a00, a01, a10, a11, a20, a21;   // FP32 columns 0,1 of P (camera frame: not label dependent)
+    int Wi, Hi;
+    double pref[3];                       // P (ref,1) in FP64
+    double q[3];
+    double p0[3], p1[3];                  // columns 0,1 of P in FP64 (world-frame sweeps)
+    const void *tex;
+};
+
+template <int FMT, bool WORLD>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Workspace w, Consts c, float4 *planes, int *label_out,
+                                                         float *cost_out)
+{
+    const int gs = blockIdx.x;
+    const int v = __ldg(w.sp_view + gs);
+    const ViewDev &vd = w.views[v];
+    const int s = gs - vd.sp_base;
+    const int n = __ldg(w.sp_cnt + gs);
+    if (n == 0) {
+        if (threadIdx.x == 0) {
+            planes[gs] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (label_out) label_out[gs] = -1;
+        }
+        return;
+    }
+    __shared__ float2 s_d[SWEEP_CHUNK];
+    __shared__ float4 s_ref[SWEEP_CHUNK];
+    __shared__ SweepPair s_pair[LFD_MAXN];
+    __shared__ double s_gh[4];            // gh and gh.(ref,1)
+    __shared__ float s_n[3];              // sweep plane normal (camera frame)
+    __shared__ float s_bc[SWEEP_THREADS / 32];
+    __shared__ int s_bk[SWEEP_THREADS / 32];
+
+    const int2 ref = __ldg(w.sp_ref + gs);
+    const int nnb = vd.nnb;
+    const int off = __ldg(w.sp_off + gs);
+    const void *own_tex = vd.quad;
+
+    if (threadIdx.x == 0) {
+        // sweep plane normal: fronto-parallel to the camera (gh = (0,0,1)) or to the
+        // world z axis; gh = K^-T n / (n . K^-1 (c,1)) so that g = z * gh
+        double gh0 = 0.0, gh1 = 0.0, gh2 = 1.0;
+        if (WORLD) {
+            const double2 cc = __ldg(w.sp_cen + gs);
+            const double *Ki = vd.Kinv;
+            double nn[3] = {vd.wz[0], vd.wz[1], vd.wz[2]};
+            const double ray[3] = {Ki[0] * cc.x + Ki[1] * cc.y + Ki[2], Ki[3] * cc.x + Ki[4] * cc.y + Ki[5],
+                                   Ki[6] * cc.x + Ki[7] * cc.y + Ki[8]};
+            double nr = nn[0] * ray[0] + nn[1] * ray[1] + nn[2] * ray[2];
+            if (nr > 0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; nr = -nr; }
+            // gh = K^-T n / (n . ray): g = z gh has inverse depth z at the centroid
+            gh0 = Ki[0] * nn[0] / nr;
+            gh1 = (Ki[1] * nn[0] + Ki[4] * nn[1]) / nr;
+            gh2 = (Ki[2] * nn[0] + Ki[5] * nn[1] + Ki[8] * nn[2]) / nr;
+            s_n[0] = (float)nn[0]; s_n[1] = (float)nn[1]; s_n[2] = (float)nn[2];
+        } else {
+            s_n[0] = 0.f; s_n[1] = 0.f; s_n[2] = -1.f;
+        }
+        s_gh[0] = gh0; s_gh[1] = gh1; s_gh[2] = gh2;
+        s_gh[3] = gh0 * ref.x + gh1 * ref.y + gh2;
+    }
+    if (threadIdx.x < nnb) {
+        const PairDev &pd = w.pairs[v * LFD_MAXN + threadIdx.x];
+        SweepPair sp;
+        sp.a00 = pd.Pf[0]; sp.a01 = pd.Pf[1];
+        sp.a10 = pd.Pf[3]; sp.a11 = pd.Pf[4];
+        sp.a20 = pd.Pf[6]; sp.a21 = pd.Pf[7];
+        sp.Wi = pd.Wi; sp.Hi = pd.Hi;
+        for (int r = 0; r < 3; r++) {
+            sp.pref[r] = pd.P[3 * r] * ref.x + pd.P[3 * r + 1] * ref.y + pd.P[3 * r + 2];
+            sp.q[r] = pd.q[r];
+            sp.p0[r] = pd.P[3 * r];
+            sp.p1[r] = pd.P[3 * r + 1];
+        }
+        sp.tex = pd.quad_i;
+        s_pair[threadIdx.x] = sp;
+    }
+    __syncthreads();
+
+    const float T = c.T;
+    float best_cost = INFINITY;
+    int best_k = 0x7fffffff;
+    for (int k0 = 0; k0 < c.L; k0 += SWEEP_THREADS) {
+        const int k = k0 + threadIdx.x;
+        const bool active = k < c.L;
+        const double u = c.jitter ? jitter_u(c.seed, c.lf_index, v, s, active ? k : 0) : 0.5;
+        const double z = c.inv_dmax + ((double)(active ? k : 0) + u) * c.delta;
+        float cost = 0.f;
+        for (int pc = 0; pc < n; pc += SWEEP_CHUNK) {
+            const int cn = min(SWEEP_CHUNK, n - pc);
+            __syncthreads();
+            for (int i = threadIdx.x; i < cn; i += SWEEP_THREADS) {
+                const unsigned pk = __ldg(w.sp_pix + off + pc + i);
+                const int x = pk & 0xffff, y = pk >> 16;
+                s_d[i] = make_float2((float)(x - ref.x), (float)(y - ref.y));
+                const float3 rc = texel_colour<FMT>(own_tex, (long long)y * vd.W + x);
+                float front = 1.f;
+                if (WORLD) front = (s_gh[0] * x + s_gh[1] * y + s_gh[2]) > 0.0 ? 1.f : 0.f;
+                s_ref[i] = make_float4(rc.x, rc.y, rc.z, front);
+            }
+            __syncthreads();
+            for (int j = 0; j < nnb; j++) {
+                const SweepPair &sp = s_pair[j];
+                // FP64 composition of the label's homography, anchored at ref
+                const double zq0 = z * sp.q[0], zq1 = z * sp.q[1], zq2 = z * sp.q[2];
+                const float cx = (float)fma(zq0, s_gh[3], sp.pref[0]);
+                const float cy = (float)fma(zq1, s_gh[3], sp.pref[1]);
+                const float cw = (float)fma(zq2, s_gh[3], sp.pref[2]);
+                float a00 = sp.a00, a01 = sp.a01, a10 = sp.a10, a11 = sp.a11, a20 = sp.a20, a21 = sp.a21;
+                if (WORLD) {
+                    a00 = (float)fma(zq0, s_gh[0], sp.p0[0]); a01 = (float)fma(zq0, s_gh[1], sp.p1[0]);
+                    a10 = (float)fma(zq1, s_gh[0], sp.p0[1]); a11 = (float)fma(zq1, s_gh[1], sp.p1[1]);
+                    a20 = (float)fma(zq2, s_gh[0], sp.p0[2]); a21 = (float)fma(zq2, s_gh[1], sp.p1[2]);
+                }
+                const void *tex = sp.tex;
+                const int Wi = sp.Wi, Hi = sp.Hi;
+#pragma unroll 4
+                for (int i = 0; i < cn; i++) {
+                    const float2 d = s_d[i];
+                    const float4 rc = s_ref[i];
+                    const float X = fmaf(a00, d.x, fmaf(a01, d.y, cx));
+                    const float Y = fmaf(a10, d.x, fmaf(a11, d.y, cy));
+                    const float Wz = fmaf(a20, d.x, fmaf(a21, d.y, cw));
+                    float t = tssd_sample<FMT>(tex, Wi, Hi, X, Y, Wz, make_float3(rc.x, rc.y, rc.z), T);
+                    if (WORLD && rc.w == 0.f) t = T;
+                    cost += t;
+                }
+            }
+        }
+        if (active) {
+            if (cost_out) cost_out[(long long)gs * c.L + k] = cost * c.col_scale * c.col_scale;
+            if (cost < best_cost) {   // k increases within a thread: strict < keeps the lowest k
+                best_cost = cost;
+                best_k = k;
+            }
+        }
+    }
+    // block arg-min, lowest k on ties
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oc = __shfl_xor_sync(0xffffffffu, best_cost, o);
+        const int ok = __shfl_xor_sync(0xffffffffu, best_k, o);
+        if (oc < best_cost || (oc == best_cost && ok < best_k)) {
+            best_cost = oc;
+            best_k = ok;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_bc[wid] = best_cost;
+        s_bk[wid] = best_k;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float bc = s_bc[0];
+        int bk = s_bk[0];
+        for (int i = 1; i < SWEEP_THREADS / 32; i++)
+            if (s_bc[i] < bc || (s_bc[i] == bc && s_bk[i] < bk)) {
+                bc = s_bc[i];
+                bk = s_bk[i];
+            }
+        const double u = c.jitter ? jitter_u(c.seed, c.lf_index, v, s, bk) : 0.5;
+        const double z = c.inv_dmax + ((double)bk + u) * c.delta;
+        planes[gs] = make_float4((float)(1.0 / z), s_n[0], s_n[1], s_n[2]);
+        if (label_out) label_out[gs] = bk;
+        atomicAdd(&w.ctr->hyp, (unsigned long long)c.L);
+        atomicAdd(&w.ctr->samples, (unsigned long long)c.L * n * nnb);
+    }
+}
+
+cudaError_t launch_sweep(const Workspace &w, const Consts &c, float4 *planes, int *label, float *cost, cudaStream_t st)
+{
+    const dim3 grid(w.S_total), block(SWEEP_THREADS);
+#define LFD_SWEEP_CASE(F)                                                                              \
+    case F:                                                                                            \
+        if (c.sweep_frame) k_sweep<F, true><<<grid, block, 0, st>>>(w, c, planes, label, cost);       \
+        else k_sweep<F, false><<<grid, block, 0, st>>>(w, c, planes, label, cost);                    \
+        break;
+    switch (c.fmt) {
+        LFD_SWEEP_CASE(LFD_RGBA8)
+        LFD_SWEEP_CASE(LFD_RGBA_F16)
+        LFD_SWEEP_CASE(LFD_RGBA_BF16)
+        LFD_SWEEP_CASE(LFD_RGBA_F32)
+    default: return cudaErrorInvalidValue;
+    }
+#undef LFD_SWEEP_CASE
+    return cudaGetLastError();
+}
+
+}  // namespace lfd

@@ -1,0 +1,193 @@
+// Internal device-side layout and helpers of liblfdepth (sm_103a).
+//
+// HBM layout of one bound light field (all views of one frame):
+//   superpixels are numbered globally, gs = sp_base[v] + s;
+//   pixels of all views are numbered globally, px_base[v] + y*W + x.
+//   sp_off[gs] .. sp_off[gs+1]   range of sp_pix for superpixel gs
+//   sp_pix[]                     packed pixel (y << 16 | x), row-major order per superpixel
+//   sp_cnt, sp_ref (rounded centroid), sp_cen (FP64 centroid), sp_col {r,g,b,minw}
+//   quad textures                per pixel the 2x2 block (x,y),(x+1,y),(x,y+1),(x+1,y+1),
+//                                edges clamped: one load serves a bilinear sample
+//   maps                         per pixel float4 {superpixel mean colour, depth value},
+//                                written by the rasteriser, gathered by the energy kernel
+//   sp_g / sp_rc                 per-superpixel plane coefficients of the current state
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/lfdepth.h"
+
+#define LFD_MAXN LFD_MAX_NEIGHBOR_VIEWS
+#define LFD_MAX_RADII 64
+
+namespace lfd {
+
+// status-word bits raised by kernels (read by lfd_synchronize)
+enum : int { DEV_ERR_LABEL = 1, DEV_ERR_COUNT = 2 };
+
+struct ViewDev {
+    int W, H, GW, GH;
+    int S, sp_base;
+    long long px_base;
+    int nnb;
+    int ksize_init, ksteps_init;
+    int pad0;
+    double Kinv[9];
+    double wz[3];            // world z axis in this camera's frame (R e3), for world-frame sweeps
+    const int *labels;       // caller label map (valid during lfd_set_input only)
+    void *quad;              // sampling texture (format dependent)
+    float4 *map;             // rasterised {colour, depth value}
+};
+
+// view v -> its k-th neighbour view i.  The plane with inverse-depth vector g
+// (1/depth(p) = g . (p,1)) induces the homography A(g) = P + q g^T from
+// homogeneous pixels of v to homogeneous pixels of i (Section III-B), with
+// P = K_i R_rel K_v^-1, q = K_i t_rel, R_rel = R_i R_v^T, t_rel = t_i - R_rel t_v.
+// Row 3 of A(g) p is the point's camera-i depth times g.p.
+struct PairDev {
+    int i, Wi, Hi, pad;
+    double P[9];
+    double q[3];
+    float Pf[9];
+    float qf[3];
+    const void *quad_i;
+    const float4 *map_i;
+};
+
+struct DevCounters {
+    unsigned long long hyp;
+    unsigned long long samples;
+    int status;
+    int bad_view, bad_index, pad;
+};
+
+// constant parameters of a launch
+struct Consts {
+    int V, L, fmt, domain;
+    int jitter, term_mask, sweep_frame, lf_index;
+    unsigned long long seed;
+    double d_min, d_max, inv_dmin, inv_dmax, delta;   // delta: inverse-depth bin width
+    float T;                 // Eq. 1 truncation (in the sampler's colour units squared)
+    float col_scale;         // sampler colour units -> [0,1]
+    float k_col;             // log2(e) / (2 alpha^2)     (Eq. 7)
+    float k_sig;             // log2(e) / (2 sigma^2)     (Eq. 6, Eq. 10)
+    float eta, xy_lo, xy_hi; // X/Y split factors: inverse domain X iff zeta >= D/(1+eps); depth domain X iff z <= D(1+eps)
+    int pad;
+};
+
+struct Workspace {
+    const ViewDev *views;
+    const PairDev *pairs;    // [V * LFD_MAXN]
+    const int *sp_view;      // [S_total]
+    const int *sp_off;       // [S_total + 1]
+    const int *sp_cnt;       // [S_total]
+    const unsigned *sp_pix;  // [total px]
+    const int2 *sp_ref;      // [S_total]
+    const double2 *sp_cen;   // [S_total]
+    const float4 *sp_col;    // [S_total] {r,g,b,minw}
+    const double4_32a *sp_g; // [S_total] plane g (FP64), w = 1 valid
+    const float4 *sp_rc;     // [S_total] {g.ref, g0, g1, valid} FP32 (rasteriser)
+    const short *radii;      // [V][LFD_MAX_ITER_INDEX + 1][LFD_MAX_RADII]
+    const int *radii_cnt;    // [V][LFD_MAX_ITER_INDEX + 1]
+    DevCounters *ctr;
+    int S_total;
+    long long px_total;
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// exact byte -> float through the 2^23 mantissa trick (byte c of w)
+template <int C>
+__device__ __forceinline__ float u8_to_f(unsigned w)
+{
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | C)) - 8388608.0f;
+}
+
+__device__ __forceinline__ float warp_sum(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    // Steele, Lea, Flood (OOPSLA 2014) finaliser of the golden-gamma increment
+    unsigned long long z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// uniform [0,1) jitter of label k of superpixel s of view v (Section III-B)
+__device__ __forceinline__ double jitter_u(unsigned long long seed, int lf, int v, int s, int k)
+{
+    unsigned long long key = ((((unsigned long long)lf << 12) + (unsigned long long)v) << 20) + (unsigned long long)s;
+    key = (key << 12) + (unsigned long long)k;
+    return (double)(splitmix64(seed ^ key) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Propagation-kernel cell of candidate m (Eq. 4, Fig. 3a): m = 0 own cell,
+// 1..8 the ring E NE N NW W SW S SE (y down), then 8 cells per distinct ray radius.
+__device__ __forceinline__ void ring_dir(int d, int &dx, int &dy)
+{
+    switch (d) {
+    case 0: dx = 1; dy = 0; break;
+    case 1: dx = 1; dy = -1; break;
+    case 2: dx = 0; dy = -1; break;
+    case 3: dx = -1; dy = -1; break;
+    case 4: dx = -1; dy = 0; break;
+    case 5: dx = -1; dy = 1; break;
+    case 6: dx = 0; dy = 1; break;
+    default: dx = 1; dy = 1; break;
+    }
+}
+
+}  // namespace lfd
+
+// pointer tables passed by value as kernel parameters
+struct ViewPtrs {
+    const void *p[LFD_MAX_VIEWS];
+    long long pitch[LFD_MAX_VIEWS];
+};
+struct OutPtrs {
+    float *p[LFD_MAX_VIEWS];
+};
+
+// launchers (defined in the kernel translation units); every buffer is the
+// context's flat workspace array indexed by global superpixel / pixel number
+namespace lfd {
+cudaError_t launch_sp_count(const Workspace &w, int V, int max_px, int *cnt, int4 *bbox, cudaStream_t st);
+cudaError_t launch_sp_scan(const Workspace &w, int V, const int *cnt, int *off, cudaStream_t st);
+cudaError_t launch_sp_collect(const Workspace &w, const Consts &c, const ViewPtrs &img, const int4 *bbox,
+                              const int *cnt, unsigned *pix, double2 *cen, int2 *ref, float4 *col, cudaStream_t st);
+cudaError_t launch_sp_minw(const Workspace &w, const Consts &c, float4 *col, cudaStream_t st);
+cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, const ViewPtrs &img, cudaStream_t st);
+cudaError_t launch_sweep(const Workspace &w, const Consts &c, float4 *planes, int *label, float *cost, cudaStream_t st);
+cudaError_t launch_plane_prep(const Workspace &w, const Consts &c, const float4 *planes, double4_32a *g, float4 *rc,
+                              cudaStream_t st);
+cudaError_t launch_rasterize(const Workspace &w, const Consts &c, const OutPtrs *depth, cudaStream_t st);
+cudaError_t launch_propagate(const Workspace &w, const Consts &c, int iter_eff, const float4 *planes_in,
+                             float4 *planes_out, int *choice, float *energy, cudaStream_t st);
+cudaError_t launch_score(const Workspace &w, const Consts &c, const float4 *planes_state, int nq, const lfd_query *q,
+                         float *out, cudaStream_t st);
+}  // namespace lfd

@@ -1,0 +1,365 @@
+"""Python binding of liblfdepth (include/lfdepth.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts torch
+tensors (device memory, streams) and numpy camera arrays into the C ABI's
+plain pointers and sizes.  Importing it loads the library and fails loudly if
+it is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lib = None
+
+MAX_NEIGHBOR_VIEWS = 8
+TERMS_HEAD = 4
+TERMS_PER_VIEW = 6
+TERMS_STRIDE = TERMS_HEAD + MAX_NEIGHBOR_VIEWS * TERMS_PER_VIEW
+
+FMT = {"rgba8": 0, "rgba_f16": 1, "rgba_bf16": 2, "rgba_f32": 3}
+_DTYPE_FMT = {torch.uint8: 0, torch.float16: 1, torch.bfloat16: 2, torch.float32: 3}
+_TEXEL = {0: 4, 1: 8, 2: 8, 3: 16}
+
+
+class Camera(C.Structure):
+    _fields_ = [("K", C.c_double * 9), ("R", C.c_double * 9), ("t", C.c_double * 3),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class LightFieldC(C.Structure):
+    _fields_ = [("num_views", C.c_int32), ("fmt", C.c_int32), ("cams", C.POINTER(Camera)),
+                ("views", C.POINTER(C.c_void_p)), ("view_pitch_bytes", C.POINTER(C.c_int64)),
+                ("labels", C.POINTER(C.c_void_p)), ("grid_w", C.POINTER(C.c_int32)),
+                ("grid_h", C.POINTER(C.c_int32))]
+
+
+class Params(C.Structure):
+    _fields_ = [("d_min", C.c_double), ("d_max", C.c_double), ("num_labels", C.c_int32),
+                ("iterations", C.c_int32), ("T", C.c_double), ("sigma", C.c_double), ("alpha", C.c_double),
+                ("eta", C.c_double), ("kernel_size_init", C.c_int32), ("kernel_step_sp", C.c_double),
+                ("max_neighbor_views", C.c_int32), ("depth_domain", C.c_int32), ("jitter", C.c_int32),
+                ("term_mask", C.c_uint32), ("sweep_frame", C.c_int32), ("seed", C.c_uint64),
+                ("lf_index", C.c_int32), ("xy_eps", C.c_double), ("warm_iter_offset", C.c_int32)]
+
+
+class Query(C.Structure):
+    _fields_ = [("view", C.c_int32), ("sp", C.c_int32), ("d", C.c_float), ("nx", C.c_float),
+                ("ny", C.c_float), ("nz", C.c_float)]
+
+
+class LfdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lfdepth status {status}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblfdepth.so (building it first when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"liblfdepth.so not built at {path}")
+        _build.build()
+    lib = C.CDLL(path)
+    vp, i32 = C.c_void_p, C.c_int32
+    P = C.POINTER
+    lib.lfd_version.restype = i32
+    lib.lfd_struct_sizes.argtypes = [P(i32)]
+    lib.lfd_status_string.restype = C.c_char_p
+    lib.lfd_status_string.argtypes = [i32]
+    lib.lfd_last_error.restype = C.c_char_p
+    lib.lfd_last_error.argtypes = [vp]
+    lib.lfd_params_default.argtypes = [P(Params)]
+    lib.lfd_create.argtypes = [P(vp), i32, C.c_uint64]
+    lib.lfd_destroy.argtypes = [vp]
+    lib.lfd_set_input.argtypes = [vp, P(LightFieldC), P(Params), vp]
+    lib.lfd_num_superpixels.argtypes = [vp, i32, P(i32)]
+    lib.lfd_plane_sweep.argtypes = [vp, P(vp), P(vp), P(vp), vp]
+    lib.lfd_rasterize.argtypes = [vp, P(vp), P(vp), vp]
+    lib.lfd_iterate.argtypes = [vp, i32, P(vp), P(vp), P(vp), P(vp), vp]
+    lib.lfd_estimate.argtypes = [vp, P(LightFieldC), P(Params), P(vp), P(vp), P(vp), vp]
+    lib.lfd_estimate_host.argtypes = [vp, P(LightFieldC), P(Params), P(vp), P(vp), vp]
+    lib.lfd_synchronize.argtypes = [vp, vp]
+    lib.lfd_counters.argtypes = [vp, P(C.c_uint64), P(C.c_uint64), vp]
+    lib.lfd_score.argtypes = [vp, P(vp), i32, P(Query), P(C.c_float), vp]
+    lib.lfd_get_superpixels.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    lib.lfd_neighbor_views.argtypes = [P(Camera), i32, i32, P(i32), P(i32)]
+    lib.lfd_profile_enable.argtypes = [vp, i32]
+    lib.lfd_profile_read.argtypes = [vp, P(C.c_double), P(C.c_int64)]
+    lib.lfd_kernel_offsets.restype = i32
+    lib.lfd_kernel_offsets.argtypes = [i32, i32, i32, P(i32), i32]
+    for name in ("lfd_create", "lfd_destroy", "lfd_set_input", "lfd_num_superpixels", "lfd_plane_sweep",
+                 "lfd_rasterize", "lfd_iterate", "lfd_estimate", "lfd_estimate_host", "lfd_synchronize",
+                 "lfd_counters", "lfd_score", "lfd_get_superpixels", "lfd_neighbor_views", "lfd_profile_enable",
+                 "lfd_profile_read"):
+        getattr(lib, name).restype = i32
+    sizes = (i32 * 4)()
+    lib.lfd_struct_sizes(sizes)
+    want = [C.sizeof(Camera), C.sizeof(LightFieldC), C.sizeof(Params), C.sizeof(Query)]
+    if list(sizes) != want:
+        raise RuntimeError(f"lfdepth ABI mismatch: library struct sizes {list(sizes)} != binding {want}")
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# host-logic entry points (no GPU needed)
+# ---------------------------------------------------------------------------
+
+def make_cameras(K, R, t, W, H):
+    V = len(K)
+    cams = (Camera * V)()
+    for v in range(V):
+        cams[v].K[:] = [float(x) for x in np.asarray(K[v], dtype=np.float64).reshape(9)]
+        cams[v].R[:] = [float(x) for x in np.asarray(R[v], dtype=np.float64).reshape(9)]
+        cams[v].t[:] = [float(x) for x in np.asarray(t[v], dtype=np.float64).reshape(3)]
+        cams[v].width = int(W if np.isscalar(W) else W[v])
+        cams[v].height = int(H if np.isscalar(H) else H[v])
+    return cams
+
+
+def neighbor_views(K, R, t, W, H, max_k: int = 0) -> np.ndarray:
+    lib = load()
+    cams = make_cameras(K, R, t, W, H)
+    V = len(K)
+    out = (C.c_int32 * (V * MAX_NEIGHBOR_VIEWS))()
+    k = C.c_int32()
+    st = lib.lfd_neighbor_views(cams, V, max_k, out, C.byref(k))
+    if st != 0:
+        raise LfdError(st, lib.lfd_status_string(st).decode())
+    return np.array(out, dtype=np.int32).reshape(V, MAX_NEIGHBOR_VIEWS)[:, :k.value]
+
+
+def kernel_offsets(size_init: int, steps_init: int, it: int) -> np.ndarray:
+    lib = load()
+    n = lib.lfd_kernel_offsets(size_init, steps_init, it, None, 0)
+    buf = (C.c_int32 * (2 * n))()
+    lib.lfd_kernel_offsets(size_init, steps_init, it, buf, n)
+    return np.array(buf, dtype=np.int32).reshape(n, 2)
+
+
+def params_struct(params: dict) -> Params:
+    p = Params()
+    load().lfd_params_default(C.byref(p))
+    for k, v in params.items():
+        if k in dict(Params._fields_):
+            setattr(p, k, v if not isinstance(v, (np.integer, np.floating)) else v.item())
+    return p
+
+
+def _ptr_array(ptrs):
+    arr = (C.c_void_p * len(ptrs))()
+    for i, q in enumerate(ptrs):
+        arr[i] = q
+    return arr
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One light-field workspace on one GPU (lfd_ctx)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self.lib = load()
+        self.h = C.c_void_p()
+        self._check(self.lib.lfd_create(C.byref(self.h), device, hbm_budget), "lfd_create")
+        self.device = device
+        self._keep = []
+        self.sp_counts = None
+
+    def close(self):
+        if self.h:
+            self.lib.lfd_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            msg = self.lib.lfd_last_error(self.h).decode() if self.h else ""
+            raise LfdError(st, f"{what}: {self.lib.lfd_status_string(st).decode()}: {msg}")
+
+    # -- marshalling ---------------------------------------------------------
+    def _lightfield(self, views, labels, K, R, t, GW, GH):
+        V = len(K)
+        assert views.dim() == 4 and views.shape[0] == V and views.shape[-1] == 4
+        fmt = _DTYPE_FMT[views.dtype]
+        H, W = int(views.shape[1]), int(views.shape[2])
+        cams = make_cameras(K, R, t, W, H)
+        vptr = _ptr_array([views[v].data_ptr() for v in range(V)])
+        lptr = _ptr_array([labels[v].data_ptr() for v in range(V)])
+        pitch = (C.c_int64 * V)(*([W * _TEXEL[fmt]] * V))
+        gw = (C.c_int32 * V)(*([int(GW)] * V if np.isscalar(GW) else [int(x) for x in GW]))
+        gh = (C.c_int32 * V)(*([int(GH)] * V if np.isscalar(GH) else [int(x) for x in GH]))
+        lf = LightFieldC(V, fmt, cams, vptr, pitch, lptr, gw, gh)
+        keep = (cams, vptr, lptr, pitch, gw, gh, views, labels)
+        return lf, keep
+
+    def _layout(self, V, GW, GH):
+        gw = [int(GW)] * V if np.isscalar(GW) else [int(x) for x in GW]
+        gh = [int(GH)] * V if np.isscalar(GH) else [int(x) for x in GH]
+        self.S = np.array([a * b for a, b in zip(gw, gh)], dtype=np.int64)
+        self.sp_base = np.concatenate([[0], np.cumsum(self.S)[:-1]]).astype(np.int64)
+        self.S_total = int(self.S.sum())
+        self.V = V
+
+    def _view_ptrs(self, flat: torch.Tensor, per_sp: int):
+        assert flat.is_cuda and flat.is_contiguous()
+        es = flat.element_size()
+        base = flat.data_ptr()
+        return _ptr_array([base + int(self.sp_base[v]) * per_sp * es for v in range(self.V)])
+
+    # -- staged hot path -----------------------------------------------------
+    def set_input(self, views, labels, K, R, t, GW, GH, params: dict, stream=None):
+        """views: (V,H,W,4) cuda tensor (uint8 / float16 / bfloat16 / float32);
+        labels: (V,H,W) int32 cuda tensor."""
+        lf, keep = self._lightfield(views, labels, K, R, t, GW, GH)
+        self._layout(len(K), GW, GH)
+        self.H, self.W = int(views.shape[1]), int(views.shape[2])
+        p = params_struct(params)
+        self._keep = [keep, p]
+        self._check(self.lib.lfd_set_input(self.h, C.byref(lf), C.byref(p), _stream(stream)), "lfd_set_input")
+        self.params = dict(params)
+
+    def plane_sweep(self, want_labels: bool = False, want_costs: bool = False, stream=None):
+        dev = torch.device("cuda", self.device)
+        planes = torch.zeros((self.S_total, 4), dtype=torch.float32, device=dev)
+        labels = torch.zeros(self.S_total, dtype=torch.int32, device=dev) if want_labels else None
+        L = int(self.params["num_labels"])
+        costs = torch.zeros((self.S_total, L), dtype=torch.float32, device=dev) if want_costs else None
+        self._check(self.lib.lfd_plane_sweep(
+            self.h, self._view_ptrs(planes, 4),
+            self._view_ptrs(labels, 1) if labels is not None else None,
+            self._view_ptrs(costs, L) if costs is not None else None, _stream(stream)), "lfd_plane_sweep")
+        return planes, labels, costs
+
+    def rasterize(self, planes: torch.Tensor, want_depth: bool = True, stream=None):
+        dev = planes.device
+        depth = torch.zeros((self.V, self.H, self.W), dtype=torch.float32, device=dev) if want_depth else None
+        dptr = _ptr_array([depth[v].data_ptr() for v in range(self.V)]) if want_depth else None
+        self._check(self.lib.lfd_rasterize(self.h, self._view_ptrs(planes.contiguous(), 4), dptr, _stream(stream)),
+                    "lfd_rasterize")
+        return depth
+
+    def iterate(self, it: int, planes_in: torch.Tensor, want_choice: bool = False, stream=None):
+        planes_in = planes_in.contiguous()
+        out = torch.empty_like(planes_in)
+        choice = torch.zeros((self.S_total, 2), dtype=torch.int32, device=planes_in.device) if want_choice else None
+        energy = torch.zeros((self.S_total, 2), dtype=torch.float32, device=planes_in.device) if want_choice else None
+        self._check(self.lib.lfd_iterate(
+            self.h, it, self._view_ptrs(planes_in, 4), self._view_ptrs(out, 4),
+            self._view_ptrs(choice, 2) if choice is not None else None,
+            self._view_ptrs(energy, 2) if energy is not None else None, _stream(stream)), "lfd_iterate")
+        return out, choice, energy
+
+    def estimate(self, views, labels, K, R, t, GW, GH, params: dict, warm=None, want_depth: bool = True,
+                 out_planes=None, out_depth=None, stream=None):
+        lf, keep = self._lightfield(views, labels, K, R, t, GW, GH)
+        self._layout(len(K), GW, GH)
+        self.H, self.W = int(views.shape[1]), int(views.shape[2])
+        p = params_struct(params)
+        self.params = dict(params)
+        dev = views.device
+        planes = out_planes if out_planes is not None else torch.zeros((self.S_total, 4), dtype=torch.float32, device=dev)
+        depth = None
+        dptr = None
+        if want_depth:
+            depth = out_depth if out_depth is not None else torch.zeros((self.V, self.H, self.W), dtype=torch.float32, device=dev)
+            dptr = _ptr_array([depth[v].data_ptr() for v in range(self.V)])
+        wptr = self._view_ptrs(warm.contiguous(), 4) if warm is not None else None
+        pp = self._view_ptrs(planes, 4)
+        self._keep = [keep, p, wptr, pp, dptr, warm]
+        self._check(self.lib.lfd_estimate(self.h, C.byref(lf), C.byref(p), wptr, pp, dptr, _stream(stream)),
+                    "lfd_estimate")
+        return planes, depth
+
+    def estimate_host(self, views_host: torch.Tensor, labels_host: torch.Tensor, K, R, t, GW, GH, params: dict,
+                      planes_host: torch.Tensor, depth_host: torch.Tensor | None, stream=None):
+        """Whole frame through lfd_estimate_host: inputs and outputs in (pinned) host memory."""
+        V = len(K)
+        self._layout(V, GW, GH)
+        self.H, self.W = int(views_host.shape[1]), int(views_host.shape[2])
+        fmt = _DTYPE_FMT[views_host.dtype]
+        cams = make_cameras(K, R, t, self.W, self.H)
+        vptr = _ptr_array([views_host[v].data_ptr() for v in range(V)])
+        lptr = _ptr_array([labels_host[v].data_ptr() for v in range(V)])
+        pitch = (C.c_int64 * V)(*([self.W * _TEXEL[fmt]] * V))
+        gw = (C.c_int32 * V)(*([int(GW)] * V))
+        gh = (C.c_int32 * V)(*([int(GH)] * V))
+        lf = LightFieldC(V, fmt, cams, vptr, pitch, lptr, gw, gh)
+        p = params_struct(params)
+        self.params = dict(params)
+        base = planes_host.data_ptr()
+        pp = _ptr_array([base + int(self.sp_base[v]) * 16 for v in range(V)])
+        dptr = _ptr_array([depth_host[v].data_ptr() for v in range(V)]) if depth_host is not None else None
+        self._keep = [cams, vptr, lptr, pitch, gw, gh, p, pp, dptr]
+        self._check(self.lib.lfd_estimate_host(self.h, C.byref(lf), C.byref(p), pp, dptr, _stream(stream)),
+                    "lfd_estimate_host")
+
+    def synchronize(self, stream=None):
+        self._check(self.lib.lfd_synchronize(self.h, _stream(stream)), "lfd_synchronize")
+
+    def counters(self, stream=None):
+        a, b = C.c_uint64(), C.c_uint64()
+        self._check(self.lib.lfd_counters(self.h, C.byref(a), C.byref(b), _stream(stream)), "lfd_counters")
+        return int(a.value), int(b.value)
+
+    STAGES = ("superpixels", "sweep", "raster", "propagate")
+
+    def profile_enable(self, on: bool = True):
+        self._check(self.lib.lfd_profile_enable(self.h, 1 if on else 0), "lfd_profile_enable")
+
+    def profile_read(self) -> dict:
+        ms = (C.c_double * 4)()
+        n = (C.c_int64 * 4)()
+        self._check(self.lib.lfd_profile_read(self.h, ms, n), "lfd_profile_read")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.STAGES)}
+
+    def score(self, state_planes: torch.Tensor, queries) -> np.ndarray:
+        qs = list(queries)
+        arr = (Query * max(len(qs), 1))()
+        for i, q in enumerate(qs):
+            arr[i] = Query(int(q[0]), int(q[1]), *map(float, q[2:6]))
+        out = np.zeros((max(len(qs), 1), TERMS_STRIDE), dtype=np.float32)
+        self._check(self.lib.lfd_score(self.h, self._view_ptrs(state_planes.contiguous(), 4), len(qs), arr,
+                                       out.ctypes.data_as(C.POINTER(C.c_float)), _stream(None)), "lfd_score")
+        return out[:len(qs)]
+
+    def get_superpixels(self, view: int) -> dict:
+        S = int(self.S[view])
+        off = np.zeros(S + 1, np.int32)
+        pix = np.zeros(self.H * self.W, np.int32)
+        stats = np.zeros((S, 8), np.float32)
+        nb = np.zeros(MAX_NEIGHBOR_VIEWS, np.int32)
+        self._check(self.lib.lfd_get_superpixels(self.h, view, off.ctypes.data, pix.ctypes.data, stats.ctypes.data,
+                                                 nb.ctypes.data, _stream(None)), "lfd_get_superpixels")
+        return dict(off=off, pix=pix, stats=stats, neighbours=nb[nb >= 0])
+
+
+def terms_dict(rec: np.ndarray, nviews: int) -> dict:
+    """Split one lfd_score record into named terms."""
+    d = dict(E=float(rec[0]), Es=float(rec[1]), Ec=float(rec[2]), tssd=float(rec[3]))
+    per = rec[TERMS_HEAD:TERMS_HEAD + nviews * TERMS_PER_VIEW].reshape(nviews, TERMS_PER_VIEW)
+    d.update(S=per[:, 0], Vt=per[:, 1], O=per[:, 2], nvalid=per[:, 3], nx=per[:, 4], ny=per[:, 5])
+    return d
