@@ -36,6 +36,10 @@ namespace lfd {
 typedef double4_32a dbl4;
 
 constexpr int PROP_WARPS = 4;
+#ifndef LFD_PROP_MIN_BLOCKS
+#define LFD_PROP_MIN_BLOCKS 7
+#endif
+constexpr int PROP_MIN_BLOCKS = LFD_PROP_MIN_BLOCKS;   // resident CTAs per SM the register budget targets
 constexpr int PM = 8;   // pixels per lane held in registers (256 per warp)
 
 // ---------------------------------------------------------------------------
@@ -127,32 +131,57 @@ cudaError_t launch_rasterize(const Workspace &w, const Consts &c, const OutPtrs 
 // ---------------------------------------------------------------------------
 // energy evaluation shared by the propagation and score kernels
 // ---------------------------------------------------------------------------
+//
+// Per warp (one superpixel), shared memory holds what does not change across
+// hypotheses: for each neighbour view k the homography pieces anchored at an
+// integer pixel (xa, ya) near the projection of the superpixel's reference
+// pixel under its current plane (composed in FP64, stored in FP32), and for
+// each 8-neighbour its depth, centroid and colour weight.  A hypothesis g is
+// then applied with FP32 arithmetic on small quantities only:
+//   dg = g.(ref,1) - g_a.(ref,1)  (FP64 difference, rounded once),
+//   hw = hw_a + q_z dg,   cx = Ex + Dx dg,   cy = Ey + Dy dg,
+//   per pixel offset (du,dv) from ref:
+//     Nw = hw + a20 du + a21 dv,  x = xa + (cx + b0 du + b1 dv)/Nw, ...
+// which keeps the sub-pixel position of neighbouring hypotheses to ~1e-6 px.
+
+struct alignas(16) SpView {
+    float hw_a, qw, Ex, Dx;
+    float Ey, Dy, lo_x, hi_x;            // window of fx: [-xa, Wi-1-xa]
+    float Pp00, Pp01, Pp10, Pp11;        // P00 - xa P20, P01 - xa P21, P10 - ya P20, P11 - ya P21
+    float P20, P21, lo_y, hi_y;
+    int xa, ya, Wi, pad;
+    const float4 *map;
+    long long pad2;
+};
+
+struct alignas(16) SpNb {
+    double invd, d, cx, cy;              // neighbour's current depth (inverse, metric) and centroid
+    double Px, Py, Pz;                   // its centroid point d K^-1 (c,1) (Fig. 3b vertices)
+    float w;                             // colour weight exp(-(a_j - min a))
+    int ok;
+};
+
+struct alignas(16) SpShared {
+    float2 px[32 * PM];                  // pixel offsets from ref of the first 32*PM pixels
+    SpView view[LFD_MAXN];
+    SpNb nb[8];
+    double cx, cy, rx, ry, rz, rn, grefa;        // centroid, its ray K^-1(c,1), |ray|, anchor g.(ref,1)
+    double best_ig;                              // winning candidate (propagation / refinement)
+    float bnx, bny, bnz;
+    int best_m;
+};
+
+// candidate planes of one 32-wide batch (propagation) or the 8 triangles (refinement)
+struct alignas(16) CandShared {
+    double g0[32], g1[32], g2[32], ig[32];
+    float nx[32], ny[32], nz[32];
+};
 
 struct WarpSP {
     int gs, v, s, n, off, nnb, gx, gy;
     int2 ref;
-    float cr, cg, cb, minw;
-    double cx, cy;
-    double rx, ry, rz, rn;       // own centroid ray K^-1 (c,1) and its length
-    // neighbour j = lane (< 8) for E_s and the triangles of Fig. 3b
-    bool nb_ok;
-    float nb_w;                  // colour weight exp(-(a_j - min a))
-    double nb_d, nb_invd, nb_cx, nb_cy;
-    double Px, Py, Pz;           // neighbour centroid point d_j K^-1 (c_j,1)
-    float sum_w;
-    // neighbour view k = lane (< nnb)
-    double pref0, pref1, pref2, q0, q1, q2;
-    float P00, P01, P10, P11, P20, P21, q0f, q1f, q2f;
-    int Wi, Hi;
-    const float4 *map;
-    // pixels of the first chunk
-    float du[PM], dv[PM];
-};
-
-struct ViewK {
-    float hw, a20, a21, cx, b0, b1, cy, c0, c1;
-    int xi, yi, Wi, Hi;
-    const float4 *map;
+    float cr, cg, cb, minw, sum_w;
+    const float2 *px;                    // this warp's pixel offsets (du,dv) in shared memory
 };
 
 struct Acc {
@@ -160,67 +189,77 @@ struct Acc {
     float sw, sg;
 };
 
+struct ViewK {
+    float hw, a20, a21, cx, b0, b1, cy, c0, c1, lo_x, hi_x, lo_y, hi_y;
+    int xa, ya, Wi;
+    const float4 *map;
+};
+
+// One pixel-view sample of Eq. 9-11, branch-free so that the samples of an
+// unrolled loop keep their gathers in flight together; `act` false (a lane
+// past the superpixel's last pixel) contributes nothing.
 template <int DOMAIN>
-__device__ __forceinline__ void energy_sample(const ViewK &K, float du, float dv, float gp, float cr, float cg, float cb,
-                                              const Consts &c, Acc &a)
+__device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du, float dv, float gp, float cr,
+                                              float cg, float cb, const Consts &c, Acc &a)
 {
-    if (!(gp > 0.f)) return;                                     // 3-D point not in front of camera v
     const float Nw = fmaf(K.a20, du, fmaf(K.a21, dv, K.hw));     // camera-i depth * g.p
     const float ex = fmaf(K.b0, du, fmaf(K.b1, dv, K.cx));
     const float ey = fmaf(K.c0, du, fmaf(K.c1, dv, K.cy));
     const float r = rcp_approx(Nw);
     const float fx = ex * r, fy = ey * r;                        // offsets from the integer anchor
-    const bool ok = (Nw > 0.f) && (fx >= (float)(-K.xi)) && (fx <= (float)(K.Wi - 1 - K.xi)) &&
-                    (fy >= (float)(-K.yi)) && (fy <= (float)(K.Hi - 1 - K.yi));
-    if (!ok) return;
-    const int ix = K.xi + __float2int_rd(fx + 0.5f);             // nearest pixel floor(x + 0.5)
-    const int iy = K.yi + __float2int_rd(fy + 0.5f);
-    const float4 t = __ldg(K.map + (long long)iy * K.Wi + ix);
-    a.cnt++;
+    const bool ok = act && (gp > 0.f) && (Nw > 0.f) && (fx >= K.lo_x) && (fx <= K.hi_x) && (fy >= K.lo_y) &&
+                    (fy <= K.hi_y);
+    const int ix = K.xa + __float2int_rd(fx + 0.5f);             // nearest pixel floor(x + 0.5)
+    const int iy = K.ya + __float2int_rd(fy + 0.5f);
+    const int idx = ok ? iy * K.Wi + ix : 0;                     // in-bounds address either way
+    const float4 t = __ldg(K.map + idx);
     const float dr = t.x - cr, dg = t.y - cg, db = t.z - cb;
-    a.sw += ex2_approx(-fmaf(dr, dr, fmaf(dg, dg, db * db)) * c.k_col);    // Eq. 9 summand
-    if (t.w > 0.f) {
-        float val;
-        bool inX;
-        if (DOMAIN == 0) {
-            val = gp * r;                                        // 1 / z_i(P)
-            inX = val >= t.w * c.xy_lo;
-        } else {
-            val = Nw * rcp_approx(gp);                           // z_i(P)
-            inX = val <= t.w * c.xy_hi;
-        }
-        if (inX) {
-            const float dd = val - t.w;
-            a.nx++;
-            a.sg += ex2_approx(-dd * dd * c.k_sig);              // Eq. 10 summand
-        } else {
-            a.ny++;
-        }
+    const float om = ex2_approx(-fmaf(dr, dr, fmaf(dg, dg, db * db)) * c.k_col);   // Eq. 9 summand
+    a.cnt += ok ? 1u : 0u;
+    a.sw += ok ? om : 0.f;
+    const bool has = ok && t.w > 0.f;
+    float val;
+    bool inX;
+    if (DOMAIN == 0) {
+        val = gp * r;                                            // 1 / z_i(P)
+        inX = has && val >= t.w * c.xy_lo;
+    } else {
+        val = Nw * rcp_approx(gp);                               // z_i(P)
+        inX = has && val <= t.w * c.xy_hi;
     }
+    const float dd = val - t.w;
+    const float G = ex2_approx(-dd * dd * c.k_sig);              // Eq. 10 summand
+    a.nx += inX ? 1u : 0u;
+    a.sg += inX ? G : 0.f;
+    a.ny += (has && !inX) ? 1u : 0u;
 }
 
 // E(g) for the warp's superpixel; all lanes return the same value.  When
 // `rec` is non-null lane 0 writes the terms record of lfd_score.
 template <int DOMAIN>
-__device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, double g0, double g1, double g2,
-                          int lane, float *rec)
+__device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, const SpShared &sh, double g0,
+                          double g1, double g2, int lane, float *rec)
 {
     const double gref = g0 * S.ref.x + g1 * S.ref.y + g2;
     const float g0f = (float)g0, g1f = (float)g1, grf = (float)gref;
+    const float dgr = (float)(gref - sh.grefa);
 
     // ---- smoothness (Eq. 5-7) on lanes 0..7
     float num = 0.f;
-    if (lane < 8 && S.nb_ok) {
-        const double ext = g0 * S.nb_cx + g1 * S.nb_cy + g2;     // plane's inverse depth at c_j
-        float dl;
-        bool has = true;
-        if (DOMAIN == 0) {
-            dl = (float)(S.nb_invd - ext);
-        } else {
-            has = ext > 0.0;
-            dl = has ? (float)(S.nb_d - 1.0 / ext) : 0.f;
+    if (lane < 8) {
+        const SpNb &nb = sh.nb[lane];
+        if (nb.ok) {
+            const double ext = g0 * nb.cx + g1 * nb.cy + g2;     // plane's inverse depth at c_j
+            float dl;
+            bool has = true;
+            if (DOMAIN == 0) {
+                dl = (float)(nb.invd - ext);
+            } else {
+                has = ext > 0.0;
+                dl = has ? (float)(nb.d - 1.0 / ext) : 0.f;
+            }
+            num = has ? nb.w * ex2_approx(-dl * dl * c.k_sig) : 0.f;
         }
-        num = has ? S.nb_w * ex2_approx(-dl * dl * c.k_sig) : 0.f;
     }
     num += __shfl_xor_sync(0xffffffffu, num, 4);
     num += __shfl_xor_sync(0xffffffffu, num, 2);
@@ -228,62 +267,33 @@ __device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, 
     num = __shfl_sync(0xffffffffu, num, 0);
     const float Es = S.sum_w > 0.f ? num / S.sum_w : 1.f;
 
-    // ---- per neighbour-view anchored homography (lane k composes view k)
-    ViewK mine;
-    if (lane < S.nnb) {
-        const double hx = fma(S.q0, gref, S.pref0);
-        const double hy = fma(S.q1, gref, S.pref1);
-        const double hw = fma(S.q2, gref, S.pref2);
-        const float hwf = (float)hw;
-        float xa = (float)hx / hwf, ya = (float)hy / hwf;
-        xa = fminf(fmaxf(xa, -1048576.f), 1048576.f);
-        ya = fminf(fmaxf(ya, -1048576.f), 1048576.f);
-        int xi = __float2int_rd(xa), yi = __float2int_rd(ya);
-        if (!(hwf == hwf)) { xi = 0; yi = 0; }
-        mine.hw = hwf;
-        mine.cx = (float)fma(-(double)xi, hw, hx);
-        mine.cy = (float)fma(-(double)yi, hw, hy);
-        const float a00 = fmaf(S.q0f, g0f, S.P00), a01 = fmaf(S.q0f, g1f, S.P01);
-        const float a10 = fmaf(S.q1f, g0f, S.P10), a11 = fmaf(S.q1f, g1f, S.P11);
-        mine.a20 = fmaf(S.q2f, g0f, S.P20);
-        mine.a21 = fmaf(S.q2f, g1f, S.P21);
-        mine.b0 = fmaf(-(float)xi, mine.a20, a00);
-        mine.b1 = fmaf(-(float)xi, mine.a21, a01);
-        mine.c0 = fmaf(-(float)yi, mine.a20, a10);
-        mine.c1 = fmaf(-(float)yi, mine.a21, a11);
-        mine.xi = xi;
-        mine.yi = yi;
-    }
-
-    float gp[PM];
-#pragma unroll
-    for (int j = 0; j < PM; j++) gp[j] = fmaf(g0f, S.du[j], fmaf(g1f, S.dv[j], grf));
-
     float ec = 0.f;
     for (int k = 0; k < S.nnb; k++) {
+        const SpView &sv = sh.view[k];
         ViewK K;
-        K.hw = __shfl_sync(0xffffffffu, mine.hw, k);
-        K.a20 = __shfl_sync(0xffffffffu, mine.a20, k);
-        K.a21 = __shfl_sync(0xffffffffu, mine.a21, k);
-        K.cx = __shfl_sync(0xffffffffu, mine.cx, k);
-        K.b0 = __shfl_sync(0xffffffffu, mine.b0, k);
-        K.b1 = __shfl_sync(0xffffffffu, mine.b1, k);
-        K.cy = __shfl_sync(0xffffffffu, mine.cy, k);
-        K.c0 = __shfl_sync(0xffffffffu, mine.c0, k);
-        K.c1 = __shfl_sync(0xffffffffu, mine.c1, k);
-        K.xi = __shfl_sync(0xffffffffu, mine.xi, k);
-        K.yi = __shfl_sync(0xffffffffu, mine.yi, k);
-        K.Wi = __shfl_sync(0xffffffffu, S.Wi, k);
-        K.Hi = __shfl_sync(0xffffffffu, S.Hi, k);
-        K.map = (const float4 *)__shfl_sync(0xffffffffu, (unsigned long long)S.map, k);
+        K.hw = fmaf(sv.qw, dgr, sv.hw_a);
+        K.cx = fmaf(sv.Dx, dgr, sv.Ex);
+        K.cy = fmaf(sv.Dy, dgr, sv.Ey);
+        K.b0 = fmaf(sv.Dx, g0f, sv.Pp00);
+        K.b1 = fmaf(sv.Dx, g1f, sv.Pp01);
+        K.c0 = fmaf(sv.Dy, g0f, sv.Pp10);
+        K.c1 = fmaf(sv.Dy, g1f, sv.Pp11);
+        K.a20 = fmaf(sv.qw, g0f, sv.P20);
+        K.a21 = fmaf(sv.qw, g1f, sv.P21);
+        K.lo_x = sv.lo_x; K.hi_x = sv.hi_x; K.lo_y = sv.lo_y; K.hi_y = sv.hi_y;
+        K.xa = sv.xa; K.ya = sv.ya; K.Wi = sv.Wi;
+        K.map = sv.map;
         Acc a = {0u, 0u, 0u, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < PM; j++)
-            if (lane + 32 * j < S.n) energy_sample<DOMAIN>(K, S.du[j], S.dv[j], gp[j], S.cr, S.cg, S.cb, c, a);
+        for (int j = 0; j < PM; j++) {
+            const float2 d = S.px[32 * j + lane];
+            energy_sample<DOMAIN>(K, lane + 32 * j < S.n, d.x, d.y, fmaf(g0f, d.x, fmaf(g1f, d.y, grf)), S.cr, S.cg,
+                                  S.cb, c, a);
+        }
         for (int i = 32 * PM + lane; i < S.n; i += 32) {          // pixels beyond the register chunk
             const unsigned pk = __ldg(w.sp_pix + S.off + i);
             const float du = (float)((int)(pk & 0xffff) - S.ref.x), dv = (float)((int)(pk >> 16) - S.ref.y);
-            energy_sample<DOMAIN>(K, du, dv, fmaf(g0f, du, fmaf(g1f, dv, grf)), S.cr, S.cg, S.cb, c, a);
+            energy_sample<DOMAIN>(K, true, du, dv, fmaf(g0f, du, fmaf(g1f, dv, grf)), S.cr, S.cg, S.cb, c, a);
         }
         const unsigned cnt = __reduce_add_sync(0xffffffffu, a.cnt);
         const unsigned nx = __reduce_add_sync(0xffffffffu, a.nx);
@@ -306,8 +316,11 @@ __device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, 
     return E;
 }
 
-// warp-wide set-up of the superpixel context; returns false for an empty superpixel
-__device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *planes_in, int gs, int lane, WarpSP &S)
+// Warp-wide set-up of a superpixel: registers (pixels, colour) and the warp's
+// shared record.  Returns false for an empty superpixel.  `ga` is the anchor
+// plane (the current plane when valid).
+__device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *planes_in, int gs, int lane, WarpSP &S,
+                         SpShared &sh, bool ga_valid, double ga0, double ga1, double ga2)
 {
     S.gs = gs;
     S.v = __ldg(w.sp_view + gs);
@@ -323,20 +336,25 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
     const float4 col = w.sp_col[gs];
     S.cr = col.x; S.cg = col.y; S.cb = col.z; S.minw = col.w;
     const double2 cc = w.sp_cen[gs];
-    S.cx = cc.x; S.cy = cc.y;
     const double *Ki = vd.Kinv;
-    S.rx = Ki[0] * cc.x + Ki[1] * cc.y + Ki[2];
-    S.ry = Ki[3] * cc.x + Ki[4] * cc.y + Ki[5];
-    S.rz = Ki[6] * cc.x + Ki[7] * cc.y + Ki[8];
-    S.rn = sqrt(S.rx * S.rx + S.ry * S.ry + S.rz * S.rz);
+    const double rx = Ki[0] * cc.x + Ki[1] * cc.y + Ki[2];
+    const double ry = Ki[3] * cc.x + Ki[4] * cc.y + Ki[5];
+    const double rz = Ki[6] * cc.x + Ki[7] * cc.y + Ki[8];
+    const double grefa = ga_valid ? ga0 * S.ref.x + ga1 * S.ref.y + ga2 : 0.5 * (c.inv_dmin + c.inv_dmax);
+    if (lane == 0) {
+        sh.cx = cc.x; sh.cy = cc.y;
+        sh.rx = rx; sh.ry = ry; sh.rz = rz;
+        sh.rn = sqrt(rx * rx + ry * ry + rz * rz);
+        sh.grefa = grefa;
+    }
 
-    // neighbour j = lane
-    S.nb_ok = false;
-    S.nb_w = 0.f;
-    S.nb_d = S.nb_invd = S.nb_cx = S.nb_cy = 0.0;
-    S.Px = S.Py = S.Pz = 0.0;
+    // neighbour j = lane (E_s and the triangles of Fig. 3b)
     float a = INFINITY;
     if (lane < 8) {
+        SpNb nb;
+        nb.invd = nb.d = nb.cx = nb.cy = nb.Px = nb.Py = nb.Pz = 0.0;
+        nb.ok = 0;
+        nb.w = 0.f;
         int dx, dy;
         ring_dir(lane, dx, dy);
         const int x = S.gx + dx, y = S.gy + dy;
@@ -345,65 +363,86 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
             if (__ldg(w.sp_cnt + j) > 0) {
                 const float4 pj = planes_in[j];
                 if (pj.x > 0.f && isfinite(pj.x)) {
-                    S.nb_ok = true;
+                    nb.ok = 1;
                     const float4 cj = w.sp_col[j];
                     const float dr = cj.x - S.cr, dg = cj.y - S.cg, db = cj.z - S.cb;
                     a = fmaf(dr, dr, fmaf(dg, dg, db * db)) * c.k_col;
                     const double2 c2 = w.sp_cen[j];
-                    S.nb_d = pj.x;
-                    S.nb_invd = 1.0 / (double)pj.x;
-                    S.nb_cx = c2.x;
-                    S.nb_cy = c2.y;
-                    const double rjx = Ki[0] * c2.x + Ki[1] * c2.y + Ki[2];
-                    const double rjy = Ki[3] * c2.x + Ki[4] * c2.y + Ki[5];
-                    const double rjz = Ki[6] * c2.x + Ki[7] * c2.y + Ki[8];
-                    S.Px = S.nb_d * rjx; S.Py = S.nb_d * rjy; S.Pz = S.nb_d * rjz;
+                    nb.d = pj.x;
+                    nb.invd = 1.0 / (double)pj.x;
+                    nb.cx = c2.x;
+                    nb.cy = c2.y;
+                    nb.Px = nb.d * (Ki[0] * c2.x + Ki[1] * c2.y + Ki[2]);
+                    nb.Py = nb.d * (Ki[3] * c2.x + Ki[4] * c2.y + Ki[5]);
+                    nb.Pz = nb.d * (Ki[6] * c2.x + Ki[7] * c2.y + Ki[8]);
                 }
             }
         }
+        sh.nb[lane] = nb;
     }
     float amin = a;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amin = fminf(amin, __shfl_xor_sync(0xffffffffu, amin, o));
-    S.nb_w = S.nb_ok ? ex2_approx(-(a - amin)) : 0.f;
-    float sw = S.nb_w;
-    sw += __shfl_xor_sync(0xffffffffu, sw, 4);
-    sw += __shfl_xor_sync(0xffffffffu, sw, 2);
-    sw += __shfl_xor_sync(0xffffffffu, sw, 1);
-    S.sum_w = __shfl_sync(0xffffffffu, sw, 0);
+    float wgt = (lane < 8 && a < INFINITY) ? ex2_approx(-(a - amin)) : 0.f;
+    if (lane < 8) sh.nb[lane].w = wgt;
+    wgt += __shfl_xor_sync(0xffffffffu, wgt, 4);
+    wgt += __shfl_xor_sync(0xffffffffu, wgt, 2);
+    wgt += __shfl_xor_sync(0xffffffffu, wgt, 1);
+    S.sum_w = __shfl_sync(0xffffffffu, wgt, 0);
 
-    // neighbour view k = lane
-    S.map = nullptr;
-    S.Wi = S.Hi = 0;
-    S.pref0 = S.pref1 = S.pref2 = S.q0 = S.q1 = S.q2 = 0.0;
-    S.P00 = S.P01 = S.P10 = S.P11 = S.P20 = S.P21 = S.q0f = S.q1f = S.q2f = 0.f;
+    // neighbour view k = lane: homography pieces anchored at an integer pixel (FP64 -> FP32)
     if (lane < S.nnb) {
         const PairDev &pd = w.pairs[S.v * LFD_MAXN + lane];
-        S.pref0 = pd.P[0] * S.ref.x + pd.P[1] * S.ref.y + pd.P[2];
-        S.pref1 = pd.P[3] * S.ref.x + pd.P[4] * S.ref.y + pd.P[5];
-        S.pref2 = pd.P[6] * S.ref.x + pd.P[7] * S.ref.y + pd.P[8];
-        S.q0 = pd.q[0]; S.q1 = pd.q[1]; S.q2 = pd.q[2];
-        S.P00 = pd.Pf[0]; S.P01 = pd.Pf[1];
-        S.P10 = pd.Pf[3]; S.P11 = pd.Pf[4];
-        S.P20 = pd.Pf[6]; S.P21 = pd.Pf[7];
-        S.q0f = pd.qf[0]; S.q1f = pd.qf[1]; S.q2f = pd.qf[2];
-        S.Wi = pd.Wi; S.Hi = pd.Hi;
-        S.map = pd.map_i;
+        const double pr0 = pd.P[0] * S.ref.x + pd.P[1] * S.ref.y + pd.P[2];
+        const double pr1 = pd.P[3] * S.ref.x + pd.P[4] * S.ref.y + pd.P[5];
+        const double pr2 = pd.P[6] * S.ref.x + pd.P[7] * S.ref.y + pd.P[8];
+        const double hx = fma(pd.q[0], grefa, pr0), hy = fma(pd.q[1], grefa, pr1), hw = fma(pd.q[2], grefa, pr2);
+        double xa = 0.0, ya = 0.0;
+        if (hw > 0.0) {
+            xa = floor(hx / hw);
+            ya = floor(hy / hw);
+            xa = fmin(fmax(xa, -1048576.0), 1048576.0);
+            ya = fmin(fmax(ya, -1048576.0), 1048576.0);
+        }
+        SpView sv;
+        sv.hw_a = (float)hw;
+        sv.qw = (float)pd.q[2];
+        sv.Ex = (float)(hx - xa * hw);
+        sv.Ey = (float)(hy - ya * hw);
+        sv.Dx = (float)(pd.q[0] - xa * pd.q[2]);
+        sv.Dy = (float)(pd.q[1] - ya * pd.q[2]);
+        sv.Pp00 = (float)(pd.P[0] - xa * pd.P[6]);
+        sv.Pp01 = (float)(pd.P[1] - xa * pd.P[7]);
+        sv.Pp10 = (float)(pd.P[3] - ya * pd.P[6]);
+        sv.Pp11 = (float)(pd.P[4] - ya * pd.P[7]);
+        sv.P20 = (float)pd.P[6];
+        sv.P21 = (float)pd.P[7];
+        sv.xa = (int)xa;
+        sv.ya = (int)ya;
+        sv.Wi = pd.Wi;
+        sv.lo_x = (float)(-xa);
+        sv.hi_x = (float)(pd.Wi - 1 - xa);
+        sv.lo_y = (float)(-ya);
+        sv.hi_y = (float)(pd.Hi - 1 - ya);
+        sv.map = pd.map_i;
+        sv.pad = 0;
+        sv.pad2 = 0;
+        sh.view[lane] = sv;
     }
 
-    // pixels of the register chunk
+    // pixel offsets of the first 32*PM pixels
 #pragma unroll
     for (int j = 0; j < PM; j++) {
         const int i = lane + 32 * j;
+        float2 d = make_float2(0.f, 0.f);
         if (i < S.n) {
             const unsigned pk = __ldg(w.sp_pix + S.off + i);
-            S.du[j] = (float)((int)(pk & 0xffff) - S.ref.x);
-            S.dv[j] = (float)((int)(pk >> 16) - S.ref.y);
-        } else {
-            S.du[j] = 0.f;
-            S.dv[j] = 0.f;
+            d = make_float2((float)((int)(pk & 0xffff) - S.ref.x), (float)((int)(pk >> 16) - S.ref.y));
         }
+        sh.px[i] = d;
     }
+    S.px = sh.px;
+    __syncwarp();
     return true;
 }
 
@@ -412,15 +451,21 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
 // ---------------------------------------------------------------------------
 
 template <int DOMAIN>
-__global__ void __launch_bounds__(32 * PROP_WARPS) k_propagate(Workspace w, Consts c, int iter_eff,
-                                                               const float4 *planes_in, float4 *planes_out,
-                                                               int *choice, float *energy)
+__global__ void __launch_bounds__(32 * PROP_WARPS, PROP_MIN_BLOCKS) k_propagate(Workspace w, Consts c, int iter_eff,
+                                                                                const float4 *planes_in,
+                                                                                float4 *planes_out, int *choice,
+                                                                                float *energy)
 {
-    const int gs = blockIdx.x * PROP_WARPS + (threadIdx.x >> 5);
+    __shared__ SpShared shm[PROP_WARPS];
+    __shared__ CandShared cshm[PROP_WARPS];
+    const int wid = threadIdx.x >> 5;
+    const int gs = blockIdx.x * PROP_WARPS + wid;
     const int lane = threadIdx.x & 31;
     if (gs >= w.S_total) return;
+    SpShared &sh = shm[wid];
+    const dbl4 gc = w.sp_g[gs];
     WarpSP S;
-    if (!setup_sp(w, c, planes_in, gs, lane, S)) {
+    if (!setup_sp(w, c, planes_in, gs, lane, S, sh, gc.w != 0.0, gc.x, gc.y, gc.z)) {
         if (lane == 0) {
             planes_out[gs] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (choice) { choice[2 * gs] = -1; choice[2 * gs + 1] = -1; }
@@ -429,30 +474,28 @@ __global__ void __launch_bounds__(32 * PROP_WARPS) k_propagate(Workspace w, Cons
         return;
     }
     const ViewDev &vd = w.views[S.v];
-    unsigned long long n_hyp = 0;
+    unsigned n_hyp = 0;
 
     // current plane
-    const float4 cur = planes_in[gs];
-    const dbl4 gc = w.sp_g[gs];
     float Ebest = -INFINITY;
     if (gc.w != 0.0) {
-        Ebest = evaluate<DOMAIN>(w, c, S, gc.x, gc.y, gc.z, lane, nullptr);
+        Ebest = evaluate<DOMAIN>(w, c, S, sh, gc.x, gc.y, gc.z, lane, nullptr);
         n_hyp++;
     }
-    int best_m = 0;
-    double best_ig = 0.0;
-    float bnx = cur.y, bny = cur.z, bnz = cur.w;
+    if (lane == 0) {
+        sh.best_m = 0;
+        sh.best_ig = 0.0;
+    }
 
     // propagation step: candidate planes of the kernel (Eq. 4, Fig. 3a)
     const int ii = min(iter_eff, LFD_MAX_ITER_INDEX);
     const int nr = w.radii_cnt[S.v * (LFD_MAX_ITER_INDEX + 1) + ii];
     const short *rad = w.radii + ((long long)S.v * (LFD_MAX_ITER_INDEX + 1) + ii) * LFD_MAX_RADII;
     const int M = 9 + 8 * nr;
+    CandShared &cs = cshm[wid];
     for (int base = 1; base < M; base += 32) {
         const int m = base + lane;
         bool ok = m < M;
-        double cg0 = 0, cg1 = 0, cg2 = 0, ig = 0;
-        float cnx = 0, cny = 0, cnz = 0;
         if (ok) {
             int dx, dy;
             if (m <= 8) {
@@ -471,92 +514,94 @@ __global__ void __launch_bounds__(32 * PROP_WARPS) k_propagate(Workspace w, Cons
                 ok = __ldg(w.sp_cnt + j) > 0;
                 if (ok) {
                     const dbl4 gj = w.sp_g[j];
-                    ok = gj.w != 0.0;
-                    cg0 = gj.x; cg1 = gj.y; cg2 = gj.z;
-                    ig = cg0 * S.cx + cg1 * S.cy + cg2;              // candidate's inverse depth at own centroid
-                    ok = ok && ig > 0.0 && ig >= c.inv_dmax && ig <= c.inv_dmin;
+                    const double ig = gj.x * sh.cx + gj.y * sh.cy + gj.z;   // candidate's inverse depth at own centroid
+                    ok = gj.w != 0.0 && ig > 0.0 && ig >= c.inv_dmax && ig <= c.inv_dmin;
                     const float4 pj = planes_in[j];
-                    cnx = pj.y; cny = pj.z; cnz = pj.w;
-                    const double cosr = fabs(cnx * S.rx + cny * S.ry + cnz * S.rz) / S.rn;
-                    ok = ok && cosr >= 0.1;                          // not grazing
+                    const double cosr = fabs(pj.y * sh.rx + pj.z * sh.ry + pj.w * sh.rz) / sh.rn;
+                    ok = ok && cosr >= 0.1;                                 // not grazing
+                    cs.g0[lane] = gj.x; cs.g1[lane] = gj.y; cs.g2[lane] = gj.z; cs.ig[lane] = ig;
+                    cs.nx[lane] = pj.y; cs.ny[lane] = pj.z; cs.nz[lane] = pj.w;
                 }
             }
         }
         unsigned mask = __ballot_sync(0xffffffffu, ok);
+        __syncwarp();
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            const double h0 = __shfl_sync(0xffffffffu, cg0, src);
-            const double h1 = __shfl_sync(0xffffffffu, cg1, src);
-            const double h2 = __shfl_sync(0xffffffffu, cg2, src);
-            const float E = evaluate<DOMAIN>(w, c, S, h0, h1, h2, lane, nullptr);
+            const float E = evaluate<DOMAIN>(w, c, S, sh, cs.g0[src], cs.g1[src], cs.g2[src], lane, nullptr);
             n_hyp++;
             if (E > Ebest) {
                 Ebest = E;
-                best_m = base + src;
-                best_ig = __shfl_sync(0xffffffffu, ig, src);
-                bnx = __shfl_sync(0xffffffffu, cnx, src);
-                bny = __shfl_sync(0xffffffffu, cny, src);
-                bnz = __shfl_sync(0xffffffffu, cnz, src);
+                if (lane == 0) {
+                    sh.best_m = base + src;
+                    sh.best_ig = cs.ig[src];
+                    sh.bnx = cs.nx[src];
+                    sh.bny = cs.ny[src];
+                    sh.bnz = cs.nz[src];
+                }
             }
         }
+        __syncwarp();
     }
     const float Eprop = Ebest;
+    const int best_m = sh.best_m;
 
     // refinement step: normals of the eight ring triangles (Fig. 3b)
     int best_t = -1;
-    double dnew = best_m > 0 ? 1.0 / best_ig : (double)cur.x;
+    const double dnew = best_m > 0 ? 1.0 / sh.best_ig : (double)planes_in[gs].x;
     if (Ebest > -INFINITY && dnew > 0.0) {
-        const double P0x = dnew * S.rx, P0y = dnew * S.ry, P0z = dnew * S.rz;
-        const int nxt = (lane + 1) & 7;
-        const double Qx = __shfl_sync(0xffffffffu, S.Px, nxt);
-        const double Qy = __shfl_sync(0xffffffffu, S.Py, nxt);
-        const double Qz = __shfl_sync(0xffffffffu, S.Pz, nxt);
-        const bool ok_b = __shfl_sync(0xffffffffu, S.nb_ok, nxt);
-        bool ok = lane < 8 && S.nb_ok && ok_b;
-        double tg0 = 0, tg1 = 0, tg2 = 0;
-        float tnx = 0, tny = 0, tnz = 0;
-        if (ok) {
-            const double e1x = S.Px - P0x, e1y = S.Py - P0y, e1z = S.Pz - P0z;
-            const double e2x = Qx - P0x, e2y = Qy - P0y, e2z = Qz - P0z;
-            double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-            const double nn = sqrt(nx * nx + ny * ny + nz * nz);
-            const double l1 = sqrt(e1x * e1x + e1y * e1y + e1z * e1z), l2 = sqrt(e2x * e2x + e2y * e2y + e2z * e2z);
-            ok = nn > 0.0 && nn >= 1e-12 * l1 * l2;
+        const double P0x = dnew * sh.rx, P0y = dnew * sh.ry, P0z = dnew * sh.rz;
+        bool ok = false;
+        if (lane < 8) {
+            const SpNb &A = sh.nb[lane];
+            const SpNb &B = sh.nb[(lane + 1) & 7];
+            ok = A.ok && B.ok;
             if (ok) {
-                nx /= nn; ny /= nn; nz /= nn;
-                if (nx * P0x + ny * P0y + nz * P0z > 0.0) { nx = -nx; ny = -ny; nz = -nz; }   // face the camera
-                ok = fabs(nx * S.rx + ny * S.ry + nz * S.rz) / S.rn >= 0.1;                  // not grazing
-                if (ok) ok = plane_to_g(vd, dnew, nx, ny, nz, S.cx, S.cy, tg0, tg1, tg2);
-                tnx = (float)nx; tny = (float)ny; tnz = (float)nz;
+                const double e1x = A.Px - P0x, e1y = A.Py - P0y, e1z = A.Pz - P0z;
+                const double e2x = B.Px - P0x, e2y = B.Py - P0y, e2z = B.Pz - P0z;
+                double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+                const double nn = sqrt(nx * nx + ny * ny + nz * nz);
+                const double l1 = sqrt(e1x * e1x + e1y * e1y + e1z * e1z);
+                const double l2 = sqrt(e2x * e2x + e2y * e2y + e2z * e2z);
+                ok = nn > 0.0 && nn >= 1e-12 * l1 * l2;
+                if (ok) {
+                    nx /= nn; ny /= nn; nz /= nn;
+                    if (nx * P0x + ny * P0y + nz * P0z > 0.0) { nx = -nx; ny = -ny; nz = -nz; }   // face the camera
+                    ok = fabs(nx * sh.rx + ny * sh.ry + nz * sh.rz) / sh.rn >= 0.1;              // not grazing
+                    double tg0 = 0, tg1 = 0, tg2 = 0;
+                    if (ok) ok = plane_to_g(vd, dnew, nx, ny, nz, sh.cx, sh.cy, tg0, tg1, tg2);
+                    cs.g0[lane] = tg0; cs.g1[lane] = tg1; cs.g2[lane] = tg2;
+                    cs.nx[lane] = (float)nx; cs.ny[lane] = (float)ny; cs.nz[lane] = (float)nz;
+                }
             }
         }
         unsigned mask = __ballot_sync(0xffffffffu, ok);
+        __syncwarp();
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            const double h0 = __shfl_sync(0xffffffffu, tg0, src);
-            const double h1 = __shfl_sync(0xffffffffu, tg1, src);
-            const double h2 = __shfl_sync(0xffffffffu, tg2, src);
-            const float E = evaluate<DOMAIN>(w, c, S, h0, h1, h2, lane, nullptr);
+            const float E = evaluate<DOMAIN>(w, c, S, sh, cs.g0[src], cs.g1[src], cs.g2[src], lane, nullptr);
             n_hyp++;
             if (E > Ebest) {
                 Ebest = E;
                 best_t = src;
-                bnx = __shfl_sync(0xffffffffu, tnx, src);
-                bny = __shfl_sync(0xffffffffu, tny, src);
-                bnz = __shfl_sync(0xffffffffu, tnz, src);
+                if (lane == 0) {
+                    sh.bnx = cs.nx[src];
+                    sh.bny = cs.ny[src];
+                    sh.bnz = cs.nz[src];
+                }
             }
         }
     }
     if (lane == 0) {
-        float4 out = cur;
-        if (best_t >= 0 || best_m > 0) out = make_float4((float)dnew, bnx, bny, bnz);
+        float4 out = planes_in[gs];
+        if (best_t >= 0 || best_m > 0) out = make_float4((float)dnew, sh.bnx, sh.bny, sh.bnz);
         planes_out[gs] = out;
         if (choice) { choice[2 * gs] = best_m; choice[2 * gs + 1] = best_t; }
         if (energy) { energy[2 * gs] = Eprop; energy[2 * gs + 1] = Ebest; }
-        atomicAdd(&w.ctr->hyp, n_hyp);
-        atomicAdd(&w.ctr->samples, n_hyp * (unsigned long long)S.n * S.nnb);
+        atomicAdd(&w.ctr->hyp, (unsigned long long)n_hyp);
+        atomicAdd(&w.ctr->samples, (unsigned long long)n_hyp * S.n * S.nnb);
     }
 }
 
@@ -588,19 +633,24 @@ __global__ void __launch_bounds__(128) k_score(Workspace w, Consts c, const floa
     if (lane + 32 < LFD_TERMS_STRIDE) rec[lane + 32] = 0.f;
     __syncwarp();
     const int gs = w.views[Q.view].sp_base + Q.sp;
-    WarpSP S;
-    if (!setup_sp(w, c, planes_state, gs, lane, S)) {
-        if (lane == 0) rec[0] = -INFINITY;
-        return;
-    }
-    const ViewDev &vd = w.views[S.v];
+    __shared__ SpShared shm[4];
+    SpShared &sh = shm[threadIdx.x >> 5];
+    const ViewDev &vd = w.views[Q.view];
     double g0, g1, g2;
-    if (!plane_to_g(vd, Q.d, Q.nx, Q.ny, Q.nz, S.cx, S.cy, g0, g1, g2)) {
+    bool okp = false;
+    if (__ldg(w.sp_cnt + gs) > 0) {
+        const double2 cq = w.sp_cen[gs];
+        okp = plane_to_g(vd, Q.d, Q.nx, Q.ny, Q.nz, cq.x, cq.y, g0, g1, g2);
+    }
+    if (!okp) {
         if (lane == 0) rec[0] = -INFINITY;
         return;
     }
+    const dbl4 gc = w.sp_g[gs];
+    WarpSP S;
+    setup_sp(w, c, planes_state, gs, lane, S, sh, gc.w != 0.0, gc.x, gc.y, gc.z);
     __syncwarp();
-    evaluate<DOMAIN>(w, c, S, g0, g1, g2, lane, rec);
+    evaluate<DOMAIN>(w, c, S, sh, g0, g1, g2, lane, rec);
     // truncated SSD sum of Eq. 2 for this plane (lanes over pixels)
     const double gref = g0 * S.ref.x + g1 * S.ref.y + g2;
     float tsum = 0.f;
@@ -621,7 +671,7 @@ __global__ void __launch_bounds__(128) k_score(Workspace w, Consts c, const floa
             const unsigned pk = __ldg(w.sp_pix + S.off + i);
             const int x = pk & 0xffff, y = pk >> 16;
             const float du = (float)(x - S.ref.x), dv = (float)(y - S.ref.y);
-            const float3 rc = texel_colour<FMT>(vd.quad, (long long)y * vd.W + x);
+            const float3 rc = texel_colour<FMT>(vd.quad, (long long)y * vd.W + x, (long long)vd.W * vd.H);
             const float gp = (float)(g0 * x + g1 * y + g2);
             float t = c.T;
             if (gp > 0.f) {

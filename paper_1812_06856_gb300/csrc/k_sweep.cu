@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Workspace w, Consts c, 
                 const unsigned pk = __ldg(w.sp_pix + off + pc + i);
                 const int x = pk & 0xffff, y = pk >> 16;
                 s_d[i] = make_float2((float)(x - ref.x), (float)(y - ref.y));
-                const float3 rc = texel_colour<FMT>(own_tex, (long long)y * vd.W + x);
+                const float3 rc = texel_colour<FMT>(own_tex, (long long)y * vd.W + x, (long long)vd.W * vd.H);
                 float front = 1.f;
                 if (WORLD) front = (s_gh[0] * x + s_gh[1] * y + s_gh[2]) > 0.0 ? 1.f : 0.f;
                 s_ref[i] = make_float4(rc.x, rc.y, rc.z, front);

@@ -90,7 +90,7 @@ int texel_bytes(int fmt)
 int quad_bytes(int fmt)
 {
     switch (fmt) {
-    case LFD_RGBA8: return 16;
+    case LFD_RGBA8: return 24;
     case LFD_RGBA_F16: case LFD_RGBA_BF16: return 32;
     case LFD_RGBA_F32: return 48;
     default: return 0;

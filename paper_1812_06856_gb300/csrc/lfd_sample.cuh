@@ -9,16 +9,27 @@ namespace lfd {
 template <int FMT>
 struct Quad;
 
-template <>
-struct Quad<LFD_RGBA8> {
-    float r[4], g[4], b[4];   // t00, t10, t01, t11
-    __device__ __forceinline__ void load(const void *tex, long long idx)
+// RGBA8 views are sampled from a coefficient-form texture: per pixel and
+// channel c(x+fx, y+fy) = a + fx bx + fy by + fx fy bxy with a = c00,
+// bx = c10 - c00, by = c01 - c00, bxy = c11 - c10 - c01 + c00.  All four are
+// integers of at most 11 bits, hence exact as IEEE halves: 12 halves = 24 B
+// per pixel, stored as a 16-B record (a.rgb, bx.rgb, by.rg) and an 8-B record
+// (by.b, bxy.rgb).  Values are in byte units (0..255).
+__device__ __forceinline__ float2 h2f(unsigned u);
+
+struct Coef8 {
+    float a[3], bx[3], by[3], bxy[3];
+    __device__ __forceinline__ void load(const void *tex, long long idx, long long npx)
     {
         const uint4 q = __ldg((const uint4 *)tex + idx);
-        r[0] = u8_to_f<0>(q.x); g[0] = u8_to_f<1>(q.x); b[0] = u8_to_f<2>(q.x);
-        r[1] = u8_to_f<0>(q.y); g[1] = u8_to_f<1>(q.y); b[1] = u8_to_f<2>(q.y);
-        r[2] = u8_to_f<0>(q.z); g[2] = u8_to_f<1>(q.z); b[2] = u8_to_f<2>(q.z);
-        r[3] = u8_to_f<0>(q.w); g[3] = u8_to_f<1>(q.w); b[3] = u8_to_f<2>(q.w);
+        const uint2 e = __ldg((const uint2 *)((const uint4 *)tex + npx) + idx);
+        float2 t;
+        t = h2f(q.x); a[0] = t.x; a[1] = t.y;
+        t = h2f(q.y); a[2] = t.x; bx[0] = t.y;
+        t = h2f(q.z); bx[1] = t.x; bx[2] = t.y;
+        t = h2f(q.w); by[0] = t.x; by[1] = t.y;
+        t = h2f(e.x); by[2] = t.x; bxy[0] = t.y;
+        t = h2f(e.y); bxy[1] = t.x; bxy[2] = t.y;
     }
 };
 
@@ -77,13 +88,19 @@ struct Quad<LFD_RGBA_F32> {
     }
 };
 
-// colour of pixel (x,y) itself (texel t00 of its quad)
+// colour of pixel (x,y) itself (texel t00 of its quad); npx = pixels of the view
 template <int FMT>
-__device__ __forceinline__ float3 texel_colour(const void *tex, long long idx)
+__device__ __forceinline__ float3 texel_colour(const void *tex, long long idx, long long npx)
 {
-    Quad<FMT> q;
-    q.load(tex, idx);
-    return make_float3(q.r[0], q.g[0], q.b[0]);
+    if constexpr (FMT == LFD_RGBA8) {
+        const uint4 q = __ldg((const uint4 *)tex + idx);
+        const float2 t0 = h2f(q.x), t1 = h2f(q.y);
+        return make_float3(t0.x, t0.y, t1.x);
+    } else {
+        Quad<FMT> q;
+        q.load(tex, idx);
+        return make_float3(q.r[0], q.g[0], q.b[0]);
+    }
 }
 
 // Truncated SSD of Eq. 1 between the reference colour `ref` and view i sampled
@@ -99,14 +116,25 @@ __device__ __forceinline__ float tssd_sample(const void *tex, int Wi, int Hi, fl
     if (!ok) return T;
     const float xf = floorf(x), yf = floorf(y);
     const float fx = x - xf, fy = y - yf;
-    Quad<FMT> q;
-    q.load(tex, (long long)(int)yf * Wi + (int)xf);
-    const float r0 = fmaf(fx, q.r[1] - q.r[0], q.r[0]), r1 = fmaf(fx, q.r[3] - q.r[2], q.r[2]);
-    const float g0 = fmaf(fx, q.g[1] - q.g[0], q.g[0]), g1 = fmaf(fx, q.g[3] - q.g[2], q.g[2]);
-    const float b0 = fmaf(fx, q.b[1] - q.b[0], q.b[0]), b1 = fmaf(fx, q.b[3] - q.b[2], q.b[2]);
-    const float dr = ref.x - fmaf(fy, r1 - r0, r0);
-    const float dg = ref.y - fmaf(fy, g1 - g0, g0);
-    const float db = ref.z - fmaf(fy, b1 - b0, b0);
+    const long long idx = (long long)(int)yf * Wi + (int)xf;
+    float dr, dg, db;
+    if constexpr (FMT == LFD_RGBA8) {
+        Coef8 q;
+        q.load(tex, idx, (long long)Wi * Hi);
+        const float fxy = fx * fy;
+        dr = ref.x - fmaf(fxy, q.bxy[0], fmaf(fy, q.by[0], fmaf(fx, q.bx[0], q.a[0])));
+        dg = ref.y - fmaf(fxy, q.bxy[1], fmaf(fy, q.by[1], fmaf(fx, q.bx[1], q.a[1])));
+        db = ref.z - fmaf(fxy, q.bxy[2], fmaf(fy, q.by[2], fmaf(fx, q.bx[2], q.a[2])));
+    } else {
+        Quad<FMT> q;
+        q.load(tex, idx);
+        const float r0 = fmaf(fx, q.r[1] - q.r[0], q.r[0]), r1 = fmaf(fx, q.r[3] - q.r[2], q.r[2]);
+        const float g0 = fmaf(fx, q.g[1] - q.g[0], q.g[0]), g1 = fmaf(fx, q.g[3] - q.g[2], q.g[2]);
+        const float b0 = fmaf(fx, q.b[1] - q.b[0], q.b[0]), b1 = fmaf(fx, q.b[3] - q.b[2], q.b[2]);
+        dr = ref.x - fmaf(fy, r1 - r0, r0);
+        dg = ref.y - fmaf(fy, g1 - g0, g0);
+        db = ref.z - fmaf(fy, b1 - b0, b0);
+    }
     const float ssd = fmaf(dr, dr, fmaf(dg, dg, db * db));
     return fminf(ssd, T);
 }

@@ -182,7 +182,10 @@ class Context:
         self._check(self.lib.lfd_create(C.byref(self.h), device, hbm_budget), "lfd_create")
         self.device = device
         self._keep = []
-        self.sp_counts = None
+        self.V = 0
+        self.S = np.zeros(0, np.int64)
+        self.sp_base = np.zeros(0, np.int64)
+        self.S_total = 0
 
     def close(self):
         if self.h:
@@ -226,6 +229,8 @@ class Context:
 
     def _view_ptrs(self, flat: torch.Tensor, per_sp: int):
         assert flat.is_cuda and flat.is_contiguous()
+        if self.V == 0:                      # nothing bound: the library reports the call order
+            return _ptr_array([flat.data_ptr()])
         es = flat.element_size()
         base = flat.data_ptr()
         return _ptr_array([base + int(self.sp_base[v]) * per_sp * es for v in range(self.V)])

@@ -63,6 +63,18 @@ def same_plane(a, b, rel_d=2e-6, abs_n=2e-6):
     return dd & nn
 
 
+def separated_best(E, lo, hi, best):
+    """The oracle's choice `best` is decided: its interval lies above every other
+    valid candidate's interval by more than the tie tolerance.  E/lo/hi are
+    arrays over candidates (-inf = not evaluated)."""
+    valid = np.isfinite(E)
+    valid[best] = False
+    if not valid.any():
+        return True
+    top = np.max(hi[valid])
+    return lo[best] > top + TIE_REL * abs(top) + ABS
+
+
 def admissible(E_hi_choice, E_lo_all):
     """The choice's upper bound reaches the best lower bound (within TIE_REL)."""
     best_lo = np.max(E_lo_all)
