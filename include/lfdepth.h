@@ -275,6 +275,36 @@ lfd_status lfd_score(lfd_ctx *ctx, const float *const *state_planes, int32_t nq,
 lfd_status lfd_get_superpixels(lfd_ctx *ctx, int32_t view, int32_t *offsets, int32_t *pixels, float *stats,
                                int32_t *neighbours, void *stream);
 
+/* ---- allocation-free variant -------------------------------------------- */
+
+/* The paper has no counterpart to this entry point: it serves callers that
+ * cannot allocate device memory where they need superpixel statistics, e.g.
+ * code recorded into a CUDA graph by stream capture (allocation calls are not
+ * allowed during capture), real-time loops with a fixed memory plan that may
+ * not touch the allocator once running, or hosts whose device allocator
+ * belongs to another framework.
+ *
+ * It computes, for one view, what lfd_set_input computes per superpixel and
+ * lfd_get_superpixels reports as stats: stats_out[s*8 + 0..7] = {cx, cy, r, g,
+ * b, minw, count, 0} for every label s < grid_w*grid_h (device float array of
+ * grid_w*grid_h*8, caller-owned).  labels: device int32 width x height,
+ * row-major; image: device texels of `fmt` with pitch_bytes per row (0 = tight);
+ * alpha: the colour width of Eq. 7 used for minw.  Labels outside the grid are
+ * ignored.  Asynchronous on `stream`; allocates nothing.
+ *
+ * Its scratch (per-label counts and bounding boxes) is a fixed device array of
+ * LFD_NOALLOC_MAX_LABELS entries (1.25 MiB) that every GPU which loads the
+ * library holds until exit.  More labels than that: LFD_ERR_INVALID_ARG.  All
+ * calls on a device share the array and each call clears the part it uses,
+ * so calls whose GPU work overlaps (other streams, unordered host threads)
+ * race and must be serialised.  The first call on each device looks up the
+ * array's device address with that device current: make it before any stream
+ * capture. */
+#define LFD_NOALLOC_MAX_LABELS 65536
+lfd_status lfd_superpixel_stats_noalloc(const int32_t *labels, const void *image, int32_t width, int32_t height,
+                                        int64_t pitch_bytes, int32_t fmt, int32_t grid_w, int32_t grid_h,
+                                        double alpha, float *stats_out, void *stream);
+
 /* ---- host logic (no GPU needed) ---------------------------------------- */
 
 /* N(v) for every view: out[v * LFD_MAX_NEIGHBOR_VIEWS + k], -1 padded;

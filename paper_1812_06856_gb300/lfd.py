@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True):
     lib.lfd_neighbor_views.argtypes = [P(Camera), i32, i32, P(i32), P(i32)]
     lib.lfd_profile_enable.argtypes = [vp, i32]
     lib.lfd_profile_read.argtypes = [vp, P(C.c_double), P(C.c_int64)]
+    lib.lfd_superpixel_stats_noalloc.argtypes = [vp, vp, i32, i32, C.c_int64, i32, i32, i32, C.c_double, vp, vp]
+    lib.lfd_superpixel_stats_noalloc.restype = i32
     lib.lfd_kernel_offsets.restype = i32
     lib.lfd_kernel_offsets.argtypes = [i32, i32, i32, P(i32), i32]
     for name in ("lfd_create", "lfd_destroy", "lfd_set_input", "lfd_num_superpixels", "lfd_plane_sweep",
@@ -149,6 +151,20 @@ def kernel_offsets(size_init: int, steps_init: int, it: int) -> np.ndarray:
     buf = (C.c_int32 * (2 * n))()
     lib.lfd_kernel_offsets(size_init, steps_init, it, buf, n)
     return np.array(buf, dtype=np.int32).reshape(n, 2)
+
+
+def superpixel_stats_noalloc(labels: torch.Tensor, image: torch.Tensor, grid_w: int, grid_h: int, alpha: float,
+                             stats_out: torch.Tensor, stream=None) -> None:
+    """lfd_superpixel_stats_noalloc on one view: labels (H,W) int32 and image
+    (H,W,4) on the device, stats_out (grid_w*grid_h, 8) float32 on the device."""
+    lib = load()
+    H, W = int(labels.shape[0]), int(labels.shape[1])
+    fmt = _DTYPE_FMT[image.dtype]
+    st = lib.lfd_superpixel_stats_noalloc(labels.data_ptr(), image.data_ptr(), W, H, W * _TEXEL[fmt], fmt,
+                                          int(grid_w), int(grid_h), float(alpha), stats_out.data_ptr(),
+                                          _stream(stream))
+    if st != 0:
+        raise LfdError(st, f"lfd_superpixel_stats_noalloc: {lib.lfd_status_string(st).decode()}")
 
 
 def params_struct(params: dict) -> Params:
