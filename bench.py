@@ -38,7 +38,7 @@ UNIT = "evals/s"
 L2_FLUSH_BYTES = 256 << 20
 # algorithmic FP32 operations per pixel-view sample (counted from the method's
 # arithmetic, address arithmetic excluded)
-FLOPS_PER_SAMPLE = {"sweep": 48, "propagate": 34}
+FLOPS_PER_SAMPLE = {"sweep": 46, "propagate": 35}
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 
