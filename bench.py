@@ -43,6 +43,35 @@ SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 
 
+KERNEL_SOURCES = {
+    "k_propagate": ["k_refine.cu", "lfd_sample.cuh", "lfd_internal.cuh"],
+    "k_sweep": ["k_sweep.cu", "lfd_sample.cuh", "lfd_internal.cuh"],
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1812_06856_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload_key: str):
+    """DRAM bytes per launch of `kernel` from the ncu capture recorded in
+    profiles/dram_traffic.txt, or None when the kernel's sources changed since."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload_key:
+                return float(parts[2]) if parts[3] == kernel_source_hash(kernel) else None
+    return None
+
+
 def workload_name(cfg: int, lf) -> str:
     V, W, H = lf.rig.V, lf.rig.W, lf.rig.H
     S = lf.GW * lf.GH
@@ -119,9 +148,9 @@ def measured_peaks() -> dict:
     return {}
 
 
-def build_inputs(cfg: int, device: str):
+def build_inputs(cfg: int, device: str, scale: float = 1.0):
     from paper_1812_06856_gb300 import synth
-    lf = synth.make_config(cfg, device=device)
+    lf = synth.make_config(cfg, device=device, scale=scale)
     if cfg == 3:
         views = synth.to_rgba_float(lf.rgb, torch.float16).to(device)
     else:
@@ -211,7 +240,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     from paper_1812_06856_gb300 import lfd
-    lf, views, labels, params = build_inputs(args.config, dev)
+    lf, views, labels, params = build_inputs(args.config, dev, args.scale)
     V, H, W = lf.rig.V, lf.rig.H, lf.rig.W
     ctx = lfd.Context(local)
     K, R, t, GW, GH = lf.rig.K, lf.rig.R, lf.rig.t, lf.GW, lf.GH
@@ -279,8 +308,10 @@ def run_ours(args):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    wkey = f"config{args.config}@{args.scale:g}"
     roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": recorded_traffic(f"k_{dom}", wkey),
+                "traffic_unit": "DRAM bytes per launch (ncu, profiles/dram_traffic.txt)",
                 "peak_note": f"FP32 FMA peak {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
                              f"{sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
                 "algorithmic": f"{FLOPS_PER_SAMPLE[dom]} FP32 flop per pixel-view sample x "
@@ -351,10 +382,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--scale", type=float, default=1.0, help="resolution scale (small cases for profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=float, default=0.02, help="superpixel fraction timed on the CPU oracle")
+    ap.add_argument("--cpu-sample", type=float, default=0.25, help="superpixel fraction timed on the CPU oracle")
     ap.add_argument("--ref-sample", type=float, default=0.004, help="superpixel fraction per reference step")
     args = ap.parse_args()
     if args.warmup < 3:

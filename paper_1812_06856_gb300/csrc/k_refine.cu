@@ -295,12 +295,19 @@ __device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, 
             const float du = (float)((int)(pk & 0xffff) - S.ref.x), dv = (float)((int)(pk >> 16) - S.ref.y);
             energy_sample<DOMAIN>(K, true, du, dv, fmaf(g0f, du, fmaf(g1f, dv, grf)), S.cr, S.cg, S.cb, c, a);
         }
-        const unsigned cnt = __reduce_add_sync(0xffffffffu, a.cnt);
-        const unsigned nx = __reduce_add_sync(0xffffffffu, a.nx);
+        unsigned cnt, nx;
+        if (S.n < 65536) {    // counts fit 16 bits: one REDUX for |Omega_i| and |X_i|
+            const unsigned cx2 = __reduce_add_sync(0xffffffffu, a.cnt | (a.nx << 16));
+            cnt = cx2 & 0xffffu;
+            nx = cx2 >> 16;
+        } else {
+            cnt = __reduce_add_sync(0xffffffffu, a.cnt);
+            nx = __reduce_add_sync(0xffffffffu, a.nx);
+        }
         const unsigned ny = __reduce_add_sync(0xffffffffu, a.ny);
         const float sw = warp_sum(a.sw), sg = warp_sum(a.sg);
-        const float Si = cnt > 0 ? sw / (float)cnt : 0.f;                                  // Eq. 9
-        const float Vi = (cnt > 0 && nx > 0) ? Si * (sg / (float)nx) : 0.f;                // Eq. 10
+        const float Si = cnt > 0 ? sw * rcp_approx((float)cnt) : 0.f;                      // Eq. 9
+        const float Vi = (cnt > 0 && nx > 0) ? Si * (sg * rcp_approx((float)nx)) : 0.f;    // Eq. 10
         const float Oi = (ny > 0 && (c.term_mask & 4)) ? c.eta * (1.f - S.minw) : 0.f;     // Eq. 11
         ec += Vi + Oi;
         if (rec && lane == 0) {
