@@ -35,8 +35,9 @@
  *  - Ownership: the caller owns every buffer it passes; the context owns its
  *    workspace (superpixel lists and statistics, sampling textures, rasterised
  *    maps, ping-pong planes) and frees it in lfd_destroy().
- *  - One context serves one light field at a time and is not thread safe;
- *    use one context per concurrent light field.
+ *  - One context serves one bound input (one light field, or n of them
+ *    through lfd_estimate_batch) at a time and is not thread safe; use one
+ *    context per concurrent input.
  */
 #ifndef LFDEPTH_H
 #define LFDEPTH_H
@@ -135,7 +136,7 @@ typedef struct lfd_ctx lfd_ctx;
 
 int32_t lfd_version(void);
 /* ABI check for bindings: writes sizeof(lfd_camera), sizeof(lfd_lightfield),
- * sizeof(lfd_params), sizeof(lfd_query) into out[0..3]. */
+ * sizeof(lfd_params), sizeof(lfd_query), sizeof(lfd_batch_options) into out[0..4]. */
 void lfd_struct_sizes(int32_t *out);
 const char *lfd_status_string(lfd_status s);
 void lfd_params_default(lfd_params *p);
@@ -227,6 +228,55 @@ lfd_status lfd_estimate(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_params
  * stream has passed it (lfd_synchronize). */
 lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const lfd_params *p,
                              float *const *planes_out_host, float *const *depth_out_host, void *stream);
+
+/* ---- batched frames --------------------------------------------------- */
+
+/* Launch options of lfd_estimate_batch (lfd_batch_options_default fills
+ * autotune 0, graph 0, sweep_threads 256, sweep_persistent 0, prop_blocks 7,
+ * prop_persistent 0). */
+typedef struct {
+    int32_t autotune;          /* 1: the first call with a new argument signature times the
+                                  sweep (128/256 threads x grid/persistent) and propagation
+                                  (7/8 CTAs per SM x grid/persistent) launch shapes on its own
+                                  input and keeps the fastest; the shape fields are then ignored */
+    int32_t graph;             /* 1: the frame's device work is captured as a CUDA graph on the
+                                  first call; a later call whose signature (every pointer, size,
+                                  camera, parameter and option) is identical replays it, reading
+                                  the current contents of the same image and label buffers.
+                                  Needs a non-default stream. */
+    int32_t sweep_threads;     /* 128 or 256 (0 = 256): labels scored in parallel per superpixel */
+    int32_t sweep_persistent;  /* 1: persistent sweep CTAs take superpixels from a queue ordered
+                                  by cost (pixels x neighbour views), most expensive first */
+    int32_t prop_blocks;       /* 7 or 8 (0 = 7) resident propagation CTAs per SM */
+    int32_t prop_persistent;   /* 1: persistent propagation warps over the same ordered queue */
+    int32_t reserved[2];       /* must be 0 */
+} lfd_batch_options;
+
+void lfd_batch_options_default(lfd_batch_options *o);
+
+/* Several light fields (e.g. the frames of several rigs) in ONE pass of the
+ * hot path (Section III-E applied across light fields): every superpixel of
+ * every view of every light field is one work item of the same sweep and
+ * propagation launches.  Each light field keeps its own cameras, neighbour
+ * views (within the light field), parameters and jitter key; results are the
+ * same as n separate lfd_estimate calls.  Light fields of one call must share
+ * the pixel format, depth_domain and sweep_frame; a light field with fewer
+ * iterations than the largest passes its planes through the remaining ones.
+ *   lfs, params:  arrays [n] (host memory); images and labels are device pointers.
+ *   planes_out:   host array [n] of host arrays [V_l] of device float4[S_v] (required).
+ *   depth_out:    host array [n] of host arrays [V_l] of device float[H*W] (nullable,
+ *                 entries nullable).
+ *   options:      NULL = defaults.
+ * After the call the context is bound to all n light fields, numbered
+ * globally (light field 0's views first) for the staged calls.  Asynchronous,
+ * except that autotuning (first call of a signature) synchronises the stream. */
+lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs, const lfd_params *params,
+                              float *const *const *planes_out, float *const *const *depth_out,
+                              const lfd_batch_options *options, void *stream);
+
+/* The launch shape in use: out[0..3] = sweep_threads, sweep_persistent,
+ * prop_blocks, prop_persistent. */
+lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out);
 
 /* Wait for the stream and report device-side check failures
  * (LFD_ERR_DEVICE_CHECK) raised by this context's kernels; clears them. */

@@ -36,10 +36,6 @@ namespace lfd {
 typedef double4_32a dbl4;
 
 constexpr int PROP_WARPS = 4;
-#ifndef LFD_PROP_MIN_BLOCKS
-#define LFD_PROP_MIN_BLOCKS 7
-#endif
-constexpr int PROP_MIN_BLOCKS = LFD_PROP_MIN_BLOCKS;   // resident CTAs per SM the register budget targets
 constexpr int PM = 8;   // pixels per lane held in registers (256 per warp)
 
 // ---------------------------------------------------------------------------
@@ -94,7 +90,7 @@ cudaError_t launch_plane_prep(const Workspace &w, const Consts &c, const float4 
 // rasteriser: warp per superpixel writes {colour, depth value} of its pixels
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(128) k_rasterize(Workspace w, Consts c, OutPtrs depth, int has_depth)
+__global__ void __launch_bounds__(128) k_rasterize(Workspace w, Consts c, float *const *depth)
 {
     const int gs = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -107,7 +103,7 @@ __global__ void __launch_bounds__(128) k_rasterize(Workspace w, Consts c, OutPtr
     const float4 col = w.sp_col[gs];
     const int2 ref = w.sp_ref[gs];
     float4 *map = vd.map;
-    float *dep = has_depth ? depth.p[v] : nullptr;
+    float *dep = depth ? depth[v] : nullptr;
     for (int i = lane; i < n; i += 32) {
         const unsigned pk = __ldg(w.sp_pix + off + i);
         const int x = pk & 0xffff, y = pk >> 16;
@@ -120,11 +116,10 @@ __global__ void __launch_bounds__(128) k_rasterize(Workspace w, Consts c, OutPtr
     }
 }
 
-cudaError_t launch_rasterize(const Workspace &w, const Consts &c, const OutPtrs *depth, cudaStream_t st)
+cudaError_t launch_rasterize(const Workspace &w, const Consts &c, float *const *depth, cudaStream_t st)
 {
-    OutPtrs none = {};
     const int blocks = (w.S_total + 3) / 4;
-    k_rasterize<<<blocks, 128, 0, st>>>(w, c, depth ? *depth : none, depth ? 1 : 0);
+    k_rasterize<<<blocks, 128, 0, st>>>(w, c, depth);
     return cudaGetLastError();
 }
 
@@ -169,6 +164,8 @@ struct alignas(16) SpShared {
     double best_ig;                              // winning candidate (propagation / refinement)
     float bnx, bny, bnz;
     int best_m;
+    float k_col, k_sig, xy_lo, xy_hi, eta;       // energy constants of the superpixel's light field
+    int term_mask;
 };
 
 // candidate planes of one 32-wide batch (propagation) or the 8 triangles (refinement)
@@ -191,6 +188,7 @@ struct Acc {
 
 struct ViewK {
     float hw, a20, a21, cx, b0, b1, cy, c0, c1, lo_x, hi_x, lo_y, hi_y;
+    float k_col, k_sig, xy;
     int xa, ya, Wi;
     const float4 *map;
 };
@@ -214,7 +212,7 @@ __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du
     const int idx = ok ? iy * K.Wi + ix : 0;                     // in-bounds address either way
     const float4 t = __ldg(K.map + idx);
     const float dr = t.x - cr, dg = t.y - cg, db = t.z - cb;
-    const float om = ex2_approx(-fmaf(dr, dr, fmaf(dg, dg, db * db)) * c.k_col);   // Eq. 9 summand
+    const float om = ex2_approx(-fmaf(dr, dr, fmaf(dg, dg, db * db)) * K.k_col);   // Eq. 9 summand
     a.cnt += ok ? 1u : 0u;
     a.sw += ok ? om : 0.f;
     const bool has = ok && t.w > 0.f;
@@ -222,13 +220,13 @@ __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du
     bool inX;
     if (DOMAIN == 0) {
         val = gp * r;                                            // 1 / z_i(P)
-        inX = has && val >= t.w * c.xy_lo;
+        inX = has && val >= t.w * K.xy;
     } else {
         val = Nw * rcp_approx(gp);                               // z_i(P)
-        inX = has && val <= t.w * c.xy_hi;
+        inX = has && val <= t.w * K.xy;
     }
     const float dd = val - t.w;
-    const float G = ex2_approx(-dd * dd * c.k_sig);              // Eq. 10 summand
+    const float G = ex2_approx(-dd * dd * K.k_sig);              // Eq. 10 summand
     a.nx += inX ? 1u : 0u;
     a.sg += inX ? G : 0.f;
     a.ny += (has && !inX) ? 1u : 0u;
@@ -258,7 +256,7 @@ __device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, 
                 has = ext > 0.0;
                 dl = has ? (float)(nb.d - 1.0 / ext) : 0.f;
             }
-            num = has ? nb.w * ex2_approx(-dl * dl * c.k_sig) : 0.f;
+            num = has ? nb.w * ex2_approx(-dl * dl * sh.k_sig) : 0.f;
         }
     }
     num += __shfl_xor_sync(0xffffffffu, num, 4);
@@ -283,6 +281,9 @@ __device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, 
         K.lo_x = sv.lo_x; K.hi_x = sv.hi_x; K.lo_y = sv.lo_y; K.hi_y = sv.hi_y;
         K.xa = sv.xa; K.ya = sv.ya; K.Wi = sv.Wi;
         K.map = sv.map;
+        K.k_col = sh.k_col;
+        K.k_sig = sh.k_sig;
+        K.xy = DOMAIN == 0 ? sh.xy_lo : sh.xy_hi;
         Acc a = {0u, 0u, 0u, 0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < PM; j++) {
@@ -308,7 +309,7 @@ __device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, 
         const float sw = warp_sum(a.sw), sg = warp_sum(a.sg);
         const float Si = cnt > 0 ? sw * rcp_approx((float)cnt) : 0.f;                      // Eq. 9
         const float Vi = (cnt > 0 && nx > 0) ? Si * (sg * rcp_approx((float)nx)) : 0.f;    // Eq. 10
-        const float Oi = (ny > 0 && (c.term_mask & 4)) ? c.eta * (1.f - S.minw) : 0.f;     // Eq. 11
+        const float Oi = (ny > 0 && (sh.term_mask & 4)) ? sh.eta * (1.f - S.minw) : 0.f;   // Eq. 11
         ec += Vi + Oi;
         if (rec && lane == 0) {
             float *r = rec + LFD_TERMS_HEAD + k * LFD_TERMS_PER_VIEW;
@@ -316,7 +317,7 @@ __device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, 
         }
     }
     const float Ec = S.nnb > 0 ? ec / (float)S.nnb : 0.f;                                  // Eq. 8
-    const float E = ((c.term_mask & 2) ? Ec : 1.f) * ((c.term_mask & 1) ? Es : 1.f);      // Eq. 3
+    const float E = ((sh.term_mask & 2) ? Ec : 1.f) * ((sh.term_mask & 1) ? Es : 1.f);    // Eq. 3
     if (rec && lane == 0) {
         rec[0] = E; rec[1] = Es; rec[2] = Ec;
     }
@@ -347,8 +348,14 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
     const double rx = Ki[0] * cc.x + Ki[1] * cc.y + Ki[2];
     const double ry = Ki[3] * cc.x + Ki[4] * cc.y + Ki[5];
     const double rz = Ki[6] * cc.x + Ki[7] * cc.y + Ki[8];
-    const double grefa = ga_valid ? ga0 * S.ref.x + ga1 * S.ref.y + ga2 : 0.5 * (c.inv_dmin + c.inv_dmax);
+    const double grefa = ga_valid ? ga0 * S.ref.x + ga1 * S.ref.y + ga2 : 0.5 * (vd.inv_dmin + vd.inv_dmax);
     if (lane == 0) {
+        sh.k_col = vd.k_col;
+        sh.k_sig = vd.k_sig;
+        sh.xy_lo = vd.xy_lo;
+        sh.xy_hi = vd.xy_hi;
+        sh.eta = vd.eta;
+        sh.term_mask = vd.term_mask;
         sh.cx = cc.x; sh.cy = cc.y;
         sh.rx = rx; sh.ry = ry; sh.rz = rz;
         sh.rn = sqrt(rx * rx + ry * ry + rz * rz);
@@ -373,7 +380,7 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
                     nb.ok = 1;
                     const float4 cj = w.sp_col[j];
                     const float dr = cj.x - S.cr, dg = cj.y - S.cg, db = cj.z - S.cb;
-                    a = fmaf(dr, dr, fmaf(dg, dg, db * db)) * c.k_col;
+                    a = fmaf(dr, dr, fmaf(dg, dg, db * db)) * vd.k_col;
                     const double2 c2 = w.sp_cen[j];
                     nb.d = pj.x;
                     nb.invd = 1.0 / (double)pj.x;
@@ -457,19 +464,23 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
 // propagation + refinement
 // ---------------------------------------------------------------------------
 
+// one Jacobi update of superpixel gs by one warp (iteration `iter`, 1-based)
 template <int DOMAIN>
-__global__ void __launch_bounds__(32 * PROP_WARPS, PROP_MIN_BLOCKS) k_propagate(Workspace w, Consts c, int iter_eff,
-                                                                                const float4 *planes_in,
-                                                                                float4 *planes_out, int *choice,
-                                                                                float *energy)
+__device__ __forceinline__ void propagate_sp(const Workspace &w, const Consts &c, int iter, int gs, int lane,
+                                             SpShared &sh, CandShared &cs, const float4 *planes_in,
+                                             float4 *planes_out, int *choice, float *energy)
 {
-    __shared__ SpShared shm[PROP_WARPS];
-    __shared__ CandShared cshm[PROP_WARPS];
-    const int wid = threadIdx.x >> 5;
-    const int gs = blockIdx.x * PROP_WARPS + wid;
-    const int lane = threadIdx.x & 31;
-    if (gs >= w.S_total) return;
-    SpShared &sh = shm[wid];
+    {
+        const ViewDev &vd0 = w.views[__ldg(w.sp_view + gs)];
+        if (c.batch_iters && iter > vd0.iters) {   // this light field has finished: carry its plane through
+            if (lane == 0) {
+                planes_out[gs] = planes_in[gs];
+                if (choice) { choice[2 * gs] = 0; choice[2 * gs + 1] = -1; }
+                if (energy) { energy[2 * gs] = -INFINITY; energy[2 * gs + 1] = -INFINITY; }
+            }
+            return;
+        }
+    }
     const dbl4 gc = w.sp_g[gs];
     WarpSP S;
     if (!setup_sp(w, c, planes_in, gs, lane, S, sh, gc.w != 0.0, gc.x, gc.y, gc.z)) {
@@ -495,11 +506,10 @@ __global__ void __launch_bounds__(32 * PROP_WARPS, PROP_MIN_BLOCKS) k_propagate(
     }
 
     // propagation step: candidate planes of the kernel (Eq. 4, Fig. 3a)
-    const int ii = min(iter_eff, LFD_MAX_ITER_INDEX);
+    const int ii = min(iter + vd.warm_off, LFD_MAX_ITER_INDEX);
     const int nr = w.radii_cnt[S.v * (LFD_MAX_ITER_INDEX + 1) + ii];
     const short *rad = w.radii + ((long long)S.v * (LFD_MAX_ITER_INDEX + 1) + ii) * LFD_MAX_RADII;
     const int M = 9 + 8 * nr;
-    CandShared &cs = cshm[wid];
     for (int base = 1; base < M; base += 32) {
         const int m = base + lane;
         bool ok = m < M;
@@ -522,7 +532,7 @@ __global__ void __launch_bounds__(32 * PROP_WARPS, PROP_MIN_BLOCKS) k_propagate(
                 if (ok) {
                     const dbl4 gj = w.sp_g[j];
                     const double ig = gj.x * sh.cx + gj.y * sh.cy + gj.z;   // candidate's inverse depth at own centroid
-                    ok = gj.w != 0.0 && ig > 0.0 && ig >= c.inv_dmax && ig <= c.inv_dmin;
+                    ok = gj.w != 0.0 && ig > 0.0 && ig >= vd.inv_dmax && ig <= vd.inv_dmin;
                     const float4 pj = planes_in[j];
                     const double cosr = fabs(pj.y * sh.rx + pj.z * sh.ry + pj.w * sh.rz) / sh.rn;
                     ok = ok && cosr >= 0.1;                                 // not grazing
@@ -612,15 +622,72 @@ __global__ void __launch_bounds__(32 * PROP_WARPS, PROP_MIN_BLOCKS) k_propagate(
     }
 }
 
-cudaError_t launch_propagate(const Workspace &w, const Consts &c, int iter_eff, const float4 *planes_in,
-                             float4 *planes_out, int *choice, float *energy, cudaStream_t st)
+template <int DOMAIN, int MINB>
+__global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate(Workspace w, Consts c, int iter,
+                                                                     const float4 *planes_in, float4 *planes_out,
+                                                                     int *choice, float *energy)
 {
-    const int blocks = (w.S_total + PROP_WARPS - 1) / PROP_WARPS;
-    if (c.domain == 0)
-        k_propagate<0><<<blocks, 32 * PROP_WARPS, 0, st>>>(w, c, iter_eff, planes_in, planes_out, choice, energy);
-    else
-        k_propagate<1><<<blocks, 32 * PROP_WARPS, 0, st>>>(w, c, iter_eff, planes_in, planes_out, choice, energy);
+    __shared__ SpShared shm[PROP_WARPS];
+    __shared__ CandShared cshm[PROP_WARPS];
+    const int wid = threadIdx.x >> 5;
+    const int gs = blockIdx.x * PROP_WARPS + wid;
+    if (gs >= w.S_total) return;
+    propagate_sp<DOMAIN>(w, c, iter, gs, threadIdx.x & 31, shm[wid], cshm[wid], planes_in, planes_out, choice, energy);
+}
+
+// persistent warps: superpixels taken from the cost-ordered queue, most expensive first
+template <int DOMAIN, int MINB>
+__global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate_persistent(Workspace w, Consts c, int iter,
+                                                                                const float4 *planes_in,
+                                                                                float4 *planes_out, int *choice,
+                                                                                float *energy)
+{
+    __shared__ SpShared shm[PROP_WARPS];
+    __shared__ CandShared cshm[PROP_WARPS];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&w.queue[1], 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= w.S_total) break;
+        propagate_sp<DOMAIN>(w, c, iter, __ldg(w.order + item), lane, shm[wid], cshm[wid], planes_in, planes_out,
+                             choice, energy);
+        __syncwarp();
+    }
+}
+
+template <int DOMAIN, int MINB>
+static cudaError_t launch_propagate_t(const Workspace &w, const Consts &c, const LaunchCfg &lc, int iter,
+                                      const float4 *planes_in, float4 *planes_out, int *choice, float *energy,
+                                      cudaStream_t st)
+{
+    if (lc.prop_persistent) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate_persistent<DOMAIN, MINB>,
+                                                                      32 * PROP_WARPS, 0);
+        if (e != cudaSuccess) return e;
+        const int warps = (w.S_total + PROP_WARPS - 1) / PROP_WARPS;
+        const int grid = max(1, min(warps, per_sm * lc.num_sms));
+        k_propagate_persistent<DOMAIN, MINB><<<grid, 32 * PROP_WARPS, 0, st>>>(w, c, iter, planes_in, planes_out,
+                                                                               choice, energy);
+    } else {
+        const int blocks = (w.S_total + PROP_WARPS - 1) / PROP_WARPS;
+        k_propagate<DOMAIN, MINB><<<blocks, 32 * PROP_WARPS, 0, st>>>(w, c, iter, planes_in, planes_out, choice,
+                                                                      energy);
+    }
     return cudaGetLastError();
+}
+
+cudaError_t launch_propagate(const Workspace &w, const Consts &c, const LaunchCfg &lc, int iter,
+                             const float4 *planes_in, float4 *planes_out, int *choice, float *energy,
+                             cudaStream_t st)
+{
+    const bool eight = lc.prop_blocks >= 8;
+    if (c.domain == 0)
+        return eight ? launch_propagate_t<0, 8>(w, c, lc, iter, planes_in, planes_out, choice, energy, st)
+                     : launch_propagate_t<0, 7>(w, c, lc, iter, planes_in, planes_out, choice, energy, st);
+    return eight ? launch_propagate_t<1, 8>(w, c, lc, iter, planes_in, planes_out, choice, energy, st)
+                 : launch_propagate_t<1, 7>(w, c, lc, iter, planes_in, planes_out, choice, energy, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -680,12 +747,12 @@ __global__ void __launch_bounds__(128) k_score(Workspace w, Consts c, const floa
             const float du = (float)(x - S.ref.x), dv = (float)(y - S.ref.y);
             const float3 rc = texel_colour<FMT>(vd.quad, (long long)y * vd.W + x, (long long)vd.W * vd.H);
             const float gp = (float)(g0 * x + g1 * y + g2);
-            float t = c.T;
+            float t = vd.T;
             if (gp > 0.f) {
                 const float X = fmaf(a00, du, fmaf(a01, dv, cx));
                 const float Y = fmaf(a10, du, fmaf(a11, dv, cy));
                 const float Wz = fmaf(a20, du, fmaf(a21, dv, cw));
-                t = tssd_sample<FMT>(pd.quad_i, pd.Wi, pd.Hi, X, Y, Wz, rc, c.T);
+                t = tssd_sample<FMT>(pd.quad_i, pd.Wi, pd.Hi, X, Y, Wz, rc, vd.T);
             }
             tsum += t;
         }

@@ -163,9 +163,8 @@ __device__ __forceinline__ T block_sum256(T v, T *sh)
     return r;
 }
 
-__global__ void __launch_bounds__(256) k_sp_collect(Workspace w, Consts c, ViewPtrs img, const int4 *bbox,
-                                                    const int *cnt, unsigned *pix, double2 *cen, int2 *ref,
-                                                    float4 *col)
+__global__ void __launch_bounds__(256) k_sp_collect(Workspace w, Consts c, const int4 *bbox, const int *cnt,
+                                                    unsigned *pix, double2 *cen, int2 *ref, float4 *col)
 {
     const int gs = blockIdx.x;
     const int v = w.sp_view[gs];
@@ -216,7 +215,7 @@ __global__ void __launch_bounds__(256) k_sp_collect(Workspace w, Consts c, ViewP
             sx += x;
             sy += y;
             double r, g, b;
-            texel_rgb(c.fmt, img.p[v], img.pitch[v], x, y, r, g, b);
+            texel_rgb(c.fmt, vd.img, vd.pitch, x, y, r, g, b);
             sr += r; sg += g; sb += b;
         }
         written += tot;
@@ -242,10 +241,10 @@ __global__ void __launch_bounds__(256) k_sp_collect(Workspace w, Consts c, ViewP
     }
 }
 
-cudaError_t launch_sp_collect(const Workspace &w, const Consts &c, const ViewPtrs &img, const int4 *bbox,
-                              const int *cnt, unsigned *pix, double2 *cen, int2 *ref, float4 *col, cudaStream_t st)
+cudaError_t launch_sp_collect(const Workspace &w, const Consts &c, const int4 *bbox, const int *cnt, unsigned *pix,
+                              double2 *cen, int2 *ref, float4 *col, cudaStream_t st)
 {
-    k_sp_collect<<<w.S_total, 256, 0, st>>>(w, c, img, bbox, cnt, pix, cen, ref, col);
+    k_sp_collect<<<w.S_total, 256, 0, st>>>(w, c, bbox, cnt, pix, cen, ref, col);
     return cudaGetLastError();
 }
 
@@ -262,7 +261,7 @@ __global__ void k_sp_minw(Workspace w, Consts c, float4 *col)
     const int s = gs - vd.sp_base;
     const int gx = s % vd.GW, gy = s / vd.GW;
     const float4 cs = col[gs];
-    // k_col = log2(e) / (2 alpha^2): omega = 2^(-|dC|^2 k_col)
+    const double k_col = vd.k_col;   // log2(e) / (2 alpha^2): omega = 2^(-|dC|^2 k_col)
     double best = 1.0;
     bool any = false;
     for (int d = 0; d < 8; d++) {
@@ -274,7 +273,7 @@ __global__ void k_sp_minw(Workspace w, Consts c, float4 *col)
         if (w.sp_cnt[j] == 0) continue;
         const float4 cj = col[j];
         const double dr = (double)cj.x - cs.x, dg = (double)cj.y - cs.y, db = (double)cj.z - cs.z;
-        const double om = exp2(-(dr * dr + dg * dg + db * db) * (double)c.k_col);
+        const double om = exp2(-(dr * dr + dg * dg + db * db) * k_col);
         if (!any || om < best) best = om;
         any = true;
     }
@@ -301,7 +300,7 @@ __device__ __forceinline__ unsigned pack_h2(float lo, float hi)
     return *reinterpret_cast<unsigned *>(&h);
 }
 
-__global__ void __launch_bounds__(256) k_quads(Workspace w, int fmt, ViewPtrs img)
+__global__ void __launch_bounds__(256) k_quads(Workspace w, int fmt)
 {
     const int v = blockIdx.y;
     const ViewDev &vd = w.views[v];
@@ -309,8 +308,8 @@ __global__ void __launch_bounds__(256) k_quads(Workspace w, int fmt, ViewPtrs im
     if (p >= vd.W * vd.H) return;
     const int x = p % vd.W, y = p / vd.W;
     const int x1 = min(x + 1, vd.W - 1), y1 = min(y + 1, vd.H - 1);
-    const char *base = (const char *)img.p[v];
-    const long long pitch = img.pitch[v];
+    const char *base = (const char *)vd.img;
+    const long long pitch = vd.pitch;
     const char *r0 = base + (long long)y * pitch;
     const char *r1 = base + (long long)y1 * pitch;
     if (fmt == LFD_RGBA8) {
@@ -345,10 +344,64 @@ __global__ void __launch_bounds__(256) k_quads(Workspace w, int fmt, ViewPtrs im
     }
 }
 
-cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, const ViewPtrs &img, cudaStream_t st)
+cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStream_t st)
 {
     dim3 grid((max_px + 255) / 256, V);
-    k_quads<<<grid, 256, 0, st>>>(w, fmt, img);
+    k_quads<<<grid, 256, 0, st>>>(w, fmt);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// 6. cost order of the superpixels for persistent launches: a counting sort by
+//    pixel count x neighbour views, most expensive first (order inside a bucket
+//    is arbitrary; every superpixel's result is independent of it)
+// ---------------------------------------------------------------------------
+
+constexpr int ORDER_BUCKETS = 1024;
+
+__device__ __forceinline__ int cost_bucket(const Workspace &w, int gs)
+{
+    const int n = __ldg(w.sp_cnt + gs);
+    const int nnb = w.views[__ldg(w.sp_view + gs)].nnb;
+    const int b = (n * nnb) >> 4;
+    return ORDER_BUCKETS - 1 - min(b, ORDER_BUCKETS - 1);      // descending cost
+}
+
+__global__ void k_order_hist(Workspace w, int *hist)
+{
+    const int gs = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gs < w.S_total) atomicAdd(&hist[cost_bucket(w, gs)], 1);
+}
+
+__global__ void __launch_bounds__(1024) k_order_scan(int *hist)
+{
+    __shared__ int sh[ORDER_BUCKETS];
+    const int t = threadIdx.x;
+    sh[t] = hist[t];
+    __syncthreads();
+    for (int o = 1; o < ORDER_BUCKETS; o <<= 1) {
+        const int v = t >= o ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += v;
+        __syncthreads();
+    }
+    hist[t] = sh[t] - hist[t];      // exclusive start of each bucket
+}
+
+__global__ void k_order_scatter(Workspace w, int *hist, int *order)
+{
+    const int gs = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gs < w.S_total) order[atomicAdd(&hist[cost_bucket(w, gs)], 1)] = gs;
+}
+
+cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * ORDER_BUCKETS, st);
+    if (e != cudaSuccess) return e;
+    const int blocks = (w.S_total + 255) / 256;
+    k_order_hist<<<blocks, 256, 0, st>>>(w, hist);
+    k_order_scan<<<1, ORDER_BUCKETS, 0, st>>>(hist);
+    k_order_scatter<<<blocks, 256, 0, st>>>(w, hist, order);
     return cudaGetLastError();
 }
 

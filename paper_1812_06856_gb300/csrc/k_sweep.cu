@@ -22,7 +22,6 @@
 
 namespace lfd {
 
-constexpr int SWEEP_THREADS = 256;
 constexpr int SWEEP_CHUNK = 128;
 
 struct SweepPair {
@@ -34,11 +33,23 @@ struct SweepPair {
     const void *tex;
 };
 
-template <int FMT, bool WORLD>
-__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Workspace w, Consts c, float4 *planes, int *label_out,
-                                                         float *cost_out)
+template <int THREADS>
+struct SweepShared {
+    float2 d[SWEEP_CHUNK];
+    float4 ref[SWEEP_CHUNK];
+    SweepPair pair[LFD_MAXN];
+    double gh[4];                         // gh and gh.(ref,1)
+    float n[3];                           // sweep plane normal (camera frame)
+    float bc[THREADS / 32];
+    int bk[THREADS / 32];
+    int item;
+};
+
+// the whole sweep of superpixel gs by one CTA (threads = labels)
+template <int FMT, bool WORLD, int THREADS>
+__device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, int gs, SweepShared<THREADS> &sh,
+                                         float4 *planes, int *label_out, float *cost_out)
 {
-    const int gs = blockIdx.x;
     const int v = __ldg(w.sp_view + gs);
     const ViewDev &vd = w.views[v];
     const int s = gs - vd.sp_base;
@@ -50,18 +61,11 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Workspace w, Consts c, 
         }
         return;
     }
-    __shared__ float2 s_d[SWEEP_CHUNK];
-    __shared__ float4 s_ref[SWEEP_CHUNK];
-    __shared__ SweepPair s_pair[LFD_MAXN];
-    __shared__ double s_gh[4];            // gh and gh.(ref,1)
-    __shared__ float s_n[3];              // sweep plane normal (camera frame)
-    __shared__ float s_bc[SWEEP_THREADS / 32];
-    __shared__ int s_bk[SWEEP_THREADS / 32];
-
     const int2 ref = __ldg(w.sp_ref + gs);
     const int nnb = vd.nnb;
     const int off = __ldg(w.sp_off + gs);
     const void *own_tex = vd.quad;
+    const int L = vd.L;
 
     if (threadIdx.x == 0) {
         // sweep plane normal: fronto-parallel to the camera (gh = (0,0,1)) or to the
@@ -75,16 +79,15 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Workspace w, Consts c, 
                                    Ki[6] * cc.x + Ki[7] * cc.y + Ki[8]};
             double nr = nn[0] * ray[0] + nn[1] * ray[1] + nn[2] * ray[2];
             if (nr > 0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; nr = -nr; }
-            // gh = K^-T n / (n . ray): g = z gh has inverse depth z at the centroid
-            gh0 = Ki[0] * nn[0] / nr;
-            gh1 = (Ki[1] * nn[0] + Ki[4] * nn[1]) / nr;
+            gh0 = (Ki[0] * nn[0] + Ki[3] * nn[1] + Ki[6] * nn[2]) / nr;
+            gh1 = (Ki[1] * nn[0] + Ki[4] * nn[1] + Ki[7] * nn[2]) / nr;
             gh2 = (Ki[2] * nn[0] + Ki[5] * nn[1] + Ki[8] * nn[2]) / nr;
-            s_n[0] = (float)nn[0]; s_n[1] = (float)nn[1]; s_n[2] = (float)nn[2];
+            sh.n[0] = (float)nn[0]; sh.n[1] = (float)nn[1]; sh.n[2] = (float)nn[2];
         } else {
-            s_n[0] = 0.f; s_n[1] = 0.f; s_n[2] = -1.f;
+            sh.n[0] = 0.f; sh.n[1] = 0.f; sh.n[2] = -1.f;
         }
-        s_gh[0] = gh0; s_gh[1] = gh1; s_gh[2] = gh2;
-        s_gh[3] = gh0 * ref.x + gh1 * ref.y + gh2;
+        sh.gh[0] = gh0; sh.gh[1] = gh1; sh.gh[2] = gh2;
+        sh.gh[3] = gh0 * ref.x + gh1 * ref.y + gh2;
     }
     if (threadIdx.x < nnb) {
         const PairDev &pd = w.pairs[v * LFD_MAXN + threadIdx.x];
@@ -100,51 +103,51 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Workspace w, Consts c, 
             sp.p1[r] = pd.P[3 * r + 1];
         }
         sp.tex = pd.quad_i;
-        s_pair[threadIdx.x] = sp;
+        sh.pair[threadIdx.x] = sp;
     }
     __syncthreads();
 
-    const float T = c.T;
+    const float T = vd.T;
     float best_cost = INFINITY;
     int best_k = 0x7fffffff;
-    for (int k0 = 0; k0 < c.L; k0 += SWEEP_THREADS) {
+    for (int k0 = 0; k0 < L; k0 += THREADS) {
         const int k = k0 + threadIdx.x;
-        const bool active = k < c.L;
-        const double u = c.jitter ? jitter_u(c.seed, c.lf_index, v, s, active ? k : 0) : 0.5;
-        const double z = c.inv_dmax + ((double)(active ? k : 0) + u) * c.delta;
+        const bool active = k < L;
+        const double u = vd.jitter ? jitter_u(vd.seed, vd.lf_index, vd.lv, s, active ? k : 0) : 0.5;
+        const double z = vd.inv_dmax + ((double)(active ? k : 0) + u) * vd.delta;
         float cost = 0.f;
         for (int pc = 0; pc < n; pc += SWEEP_CHUNK) {
             const int cn = min(SWEEP_CHUNK, n - pc);
             __syncthreads();
-            for (int i = threadIdx.x; i < cn; i += SWEEP_THREADS) {
+            for (int i = threadIdx.x; i < cn; i += THREADS) {
                 const unsigned pk = __ldg(w.sp_pix + off + pc + i);
                 const int x = pk & 0xffff, y = pk >> 16;
-                s_d[i] = make_float2((float)(x - ref.x), (float)(y - ref.y));
+                sh.d[i] = make_float2((float)(x - ref.x), (float)(y - ref.y));
                 const float3 rc = texel_colour<FMT>(own_tex, (long long)y * vd.W + x, (long long)vd.W * vd.H);
                 float front = 1.f;
-                if (WORLD) front = (s_gh[0] * x + s_gh[1] * y + s_gh[2]) > 0.0 ? 1.f : 0.f;
-                s_ref[i] = make_float4(rc.x, rc.y, rc.z, front);
+                if (WORLD) front = (sh.gh[0] * x + sh.gh[1] * y + sh.gh[2]) > 0.0 ? 1.f : 0.f;
+                sh.ref[i] = make_float4(rc.x, rc.y, rc.z, front);
             }
             __syncthreads();
             for (int j = 0; j < nnb; j++) {
-                const SweepPair &sp = s_pair[j];
+                const SweepPair &sp = sh.pair[j];
                 // FP64 composition of the label's homography, anchored at ref
                 const double zq0 = z * sp.q[0], zq1 = z * sp.q[1], zq2 = z * sp.q[2];
-                const float cx = (float)fma(zq0, s_gh[3], sp.pref[0]);
-                const float cy = (float)fma(zq1, s_gh[3], sp.pref[1]);
-                const float cw = (float)fma(zq2, s_gh[3], sp.pref[2]);
+                const float cx = (float)fma(zq0, sh.gh[3], sp.pref[0]);
+                const float cy = (float)fma(zq1, sh.gh[3], sp.pref[1]);
+                const float cw = (float)fma(zq2, sh.gh[3], sp.pref[2]);
                 float a00 = sp.a00, a01 = sp.a01, a10 = sp.a10, a11 = sp.a11, a20 = sp.a20, a21 = sp.a21;
                 if (WORLD) {
-                    a00 = (float)fma(zq0, s_gh[0], sp.p0[0]); a01 = (float)fma(zq0, s_gh[1], sp.p1[0]);
-                    a10 = (float)fma(zq1, s_gh[0], sp.p0[1]); a11 = (float)fma(zq1, s_gh[1], sp.p1[1]);
-                    a20 = (float)fma(zq2, s_gh[0], sp.p0[2]); a21 = (float)fma(zq2, s_gh[1], sp.p1[2]);
+                    a00 = (float)fma(zq0, sh.gh[0], sp.p0[0]); a01 = (float)fma(zq0, sh.gh[1], sp.p1[0]);
+                    a10 = (float)fma(zq1, sh.gh[0], sp.p0[1]); a11 = (float)fma(zq1, sh.gh[1], sp.p1[1]);
+                    a20 = (float)fma(zq2, sh.gh[0], sp.p0[2]); a21 = (float)fma(zq2, sh.gh[1], sp.p1[2]);
                 }
                 const void *tex = sp.tex;
                 const int Wi = sp.Wi, Hi = sp.Hi;
 #pragma unroll 4
                 for (int i = 0; i < cn; i++) {
-                    const float2 d = s_d[i];
-                    const float4 rc = s_ref[i];
+                    const float2 d = sh.d[i];
+                    const float4 rc = sh.ref[i];
                     const float X = fmaf(a00, d.x, fmaf(a01, d.y, cx));
                     const float Y = fmaf(a10, d.x, fmaf(a11, d.y, cy));
                     const float Wz = fmaf(a20, d.x, fmaf(a21, d.y, cw));
@@ -174,44 +177,92 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Workspace w, Consts c, 
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
-        s_bc[wid] = best_cost;
-        s_bk[wid] = best_k;
+        sh.bc[wid] = best_cost;
+        sh.bk[wid] = best_k;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float bc = s_bc[0];
-        int bk = s_bk[0];
-        for (int i = 1; i < SWEEP_THREADS / 32; i++)
-            if (s_bc[i] < bc || (s_bc[i] == bc && s_bk[i] < bk)) {
-                bc = s_bc[i];
-                bk = s_bk[i];
+        float bc = sh.bc[0];
+        int bk = sh.bk[0];
+        for (int i = 1; i < THREADS / 32; i++)
+            if (sh.bc[i] < bc || (sh.bc[i] == bc && sh.bk[i] < bk)) {
+                bc = sh.bc[i];
+                bk = sh.bk[i];
             }
-        const double u = c.jitter ? jitter_u(c.seed, c.lf_index, v, s, bk) : 0.5;
-        const double z = c.inv_dmax + ((double)bk + u) * c.delta;
-        planes[gs] = make_float4((float)(1.0 / z), s_n[0], s_n[1], s_n[2]);
+        const double u = vd.jitter ? jitter_u(vd.seed, vd.lf_index, vd.lv, s, bk) : 0.5;
+        const double z = vd.inv_dmax + ((double)bk + u) * vd.delta;
+        planes[gs] = make_float4((float)(1.0 / z), sh.n[0], sh.n[1], sh.n[2]);
         if (label_out) label_out[gs] = bk;
-        atomicAdd(&w.ctr->hyp, (unsigned long long)c.L);
-        atomicAdd(&w.ctr->samples, (unsigned long long)c.L * n * nnb);
+        atomicAdd(&w.ctr->hyp, (unsigned long long)L);
+        atomicAdd(&w.ctr->samples, (unsigned long long)L * n * nnb);
     }
 }
 
-cudaError_t launch_sweep(const Workspace &w, const Consts &c, float4 *planes, int *label, float *cost, cudaStream_t st)
+// one CTA per superpixel
+template <int FMT, bool WORLD, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_sweep(Workspace w, Consts c, float4 *planes, int *label_out,
+                                                   float *cost_out)
 {
-    const dim3 grid(w.S_total), block(SWEEP_THREADS);
-#define LFD_SWEEP_CASE(F)                                                                              \
-    case F:                                                                                            \
-        if (c.sweep_frame) k_sweep<F, true><<<grid, block, 0, st>>>(w, c, planes, label, cost);       \
-        else k_sweep<F, false><<<grid, block, 0, st>>>(w, c, planes, label, cost);                    \
-        break;
+    __shared__ SweepShared<THREADS> sh;
+    sweep_sp<FMT, WORLD, THREADS>(w, c, blockIdx.x, sh, planes, label_out, cost_out);
+}
+
+// persistent CTAs: superpixels taken from the cost-ordered queue, most expensive first
+template <int FMT, bool WORLD, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_sweep_persistent(Workspace w, Consts c, float4 *planes, int *label_out,
+                                                              float *cost_out)
+{
+    __shared__ SweepShared<THREADS> sh;
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(&w.queue[0], 1);
+        __syncthreads();
+        const int item = sh.item;
+        __syncthreads();
+        if (item >= w.S_total) break;
+        sweep_sp<FMT, WORLD, THREADS>(w, c, __ldg(w.order + item), sh, planes, label_out, cost_out);
+        __syncthreads();
+    }
+}
+
+template <int FMT, bool WORLD, int THREADS>
+static cudaError_t launch_sweep_t(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
+                                  float *cost, cudaStream_t st)
+{
+    if (lc.sweep_persistent) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_persistent<FMT, WORLD, THREADS>,
+                                                                      THREADS, 0);
+        if (e != cudaSuccess) return e;
+        const int grid = max(1, min(w.S_total, per_sm * lc.num_sms));
+        k_sweep_persistent<FMT, WORLD, THREADS><<<grid, THREADS, 0, st>>>(w, c, planes, label, cost);
+    } else {
+        k_sweep<FMT, WORLD, THREADS><<<w.S_total, THREADS, 0, st>>>(w, c, planes, label, cost);
+    }
+    return cudaGetLastError();
+}
+
+template <int FMT>
+static cudaError_t launch_sweep_f(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
+                                  float *cost, cudaStream_t st)
+{
+    if (c.sweep_frame) {
+        return lc.sweep_threads == 128 ? launch_sweep_t<FMT, true, 128>(w, c, lc, planes, label, cost, st)
+                                       : launch_sweep_t<FMT, true, 256>(w, c, lc, planes, label, cost, st);
+    }
+    return lc.sweep_threads == 128 ? launch_sweep_t<FMT, false, 128>(w, c, lc, planes, label, cost, st)
+                                   : launch_sweep_t<FMT, false, 256>(w, c, lc, planes, label, cost, st);
+}
+
+cudaError_t launch_sweep(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
+                         float *cost, cudaStream_t st)
+{
     switch (c.fmt) {
-        LFD_SWEEP_CASE(LFD_RGBA8)
-        LFD_SWEEP_CASE(LFD_RGBA_F16)
-        LFD_SWEEP_CASE(LFD_RGBA_BF16)
-        LFD_SWEEP_CASE(LFD_RGBA_F32)
+    case LFD_RGBA8: return launch_sweep_f<LFD_RGBA8>(w, c, lc, planes, label, cost, st);
+    case LFD_RGBA_F16: return launch_sweep_f<LFD_RGBA_F16>(w, c, lc, planes, label, cost, st);
+    case LFD_RGBA_BF16: return launch_sweep_f<LFD_RGBA_BF16>(w, c, lc, planes, label, cost, st);
+    case LFD_RGBA_F32: return launch_sweep_f<LFD_RGBA_F32>(w, c, lc, planes, label, cost, st);
     default: return cudaErrorInvalidValue;
     }
-#undef LFD_SWEEP_CASE
-    return cudaGetLastError();
 }
 
 }  // namespace lfd

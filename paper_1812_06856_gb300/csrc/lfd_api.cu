@@ -121,19 +121,23 @@ struct Layout {
 };
 
 }  // namespace
+struct LfInfo {
+    int first_view, V;
+    lfd_params p;
+};
 
 struct lfd_ctx {
     int device = 0;
+    int num_sms = 0;
     uint64_t budget = 0;
     std::string err;
     bool bound = false;
-    lfd_params p{};
     Consts c{};
     Layout L;
-    std::vector<lfd_camera> cams;
-    std::vector<int> nbr;
-    int nnb = 0;
+    std::vector<LfInfo> lfs;
+    std::vector<int> nbr;          // [V_total * 8] global view indices
     int fmt = 0;
+    LaunchCfg lc{256, 0, 7, 0, 0};
     // workspace
     Arena ws;
     Workspace w{};
@@ -150,6 +154,8 @@ struct lfd_ctx {
     short *d_radii = nullptr;
     int *d_radii_cnt = nullptr;
     DevCounters *d_ctr = nullptr;
+    int *d_order = nullptr, *d_hist = nullptr, *d_queue = nullptr;
+    float **d_depth_ptrs = nullptr;
     float4 *d_planesA = nullptr, *d_planesB = nullptr;
     int *d_label = nullptr, *d_choice = nullptr;
     float *d_energy = nullptr;
@@ -170,10 +176,21 @@ struct lfd_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_used;
     std::vector<cudaEvent_t> prof_free;
     long long launches[LFD_STAGES] = {0, 0, 0, 0};
-    // pinned upload staging
+    // pinned upload staging (records) and depth-pointer table
     void *h_stage = nullptr;
     size_t h_stage_cap = 0;
     cudaEvent_t ev_stage = nullptr;
+    float **h_depth = nullptr;
+    int h_depth_cap = 0;
+    cudaEvent_t ev_depth = nullptr;
+    // CUDA graph of a batched frame and the pinned depth table it reads
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gsig = 0;
+    long long glaunches[LFD_STAGES] = {0, 0, 0, 0};
+    float **h_bdepth = nullptr;
+    int h_bdepth_cap = 0;
+    cudaEvent_t ev_bdepth = nullptr;
+    uint64_t tuned_sig = 0;
 };
 
 namespace {
@@ -229,7 +246,6 @@ lfd_status check_lightfield(lfd_ctx *ctx, const lfd_lightfield *lf, bool host_me
     if (!lf->cams || !lf->views || !lf->labels || !lf->grid_w || !lf->grid_h)
         return fail(ctx, LFD_ERR_INVALID_ARG, "NULL array in the light field");
     const int tb = texel_bytes(lf->fmt);
-    long long px_total = 0;
     for (int v = 0; v < lf->num_views; v++) {
         const lfd_camera &c = lf->cams[v];
         if (c.width < 1 || c.height < 1 || c.width > LFD_MAX_DIM || c.height > LFD_MAX_DIM)
@@ -250,9 +266,7 @@ lfd_status check_lightfield(lfd_ctx *ctx, const lfd_lightfield *lf, bool host_me
             return fail(ctx, LFD_ERR_INVALID_ARG, "view %d: pitch %lld too small or not a multiple of %d", v, pitch, tb);
         if (!host_mem && (((uintptr_t)lf->views[v] % tb) || ((uintptr_t)lf->labels[v] % 4)))
             return fail(ctx, LFD_ERR_INVALID_ARG, "view %d: image or label pointer misaligned", v);
-        px_total += (long long)c.width * c.height;
     }
-    if (px_total >= (1LL << 31)) return fail(ctx, LFD_ERR_INVALID_ARG, "more than 2^31 pixels in one light field");
     return LFD_OK;
 }
 
@@ -270,35 +284,30 @@ void mat_mul(const double A[9], const double B[9], double C[9])
         for (int c = 0; c < 3; c++) C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
 }
 
-Consts make_consts(const lfd_params &p, int V, int fmt)
+// parameters of one light field into its view records
+void view_params(ViewDev &d, const lfd_params &p, int fmt, int lf)
 {
-    Consts c{};
-    c.V = V;
-    c.L = p.num_labels;
-    c.fmt = fmt;
-    c.domain = p.depth_domain;
-    c.jitter = p.jitter;
-    c.term_mask = (int)p.term_mask;
-    c.sweep_frame = p.sweep_frame;
-    c.lf_index = p.lf_index;
-    c.seed = p.seed;
-    c.d_min = p.d_min;
-    c.d_max = p.d_max;
-    c.inv_dmin = 1.0 / p.d_min;
-    c.inv_dmax = 1.0 / p.d_max;
-    c.delta = (1.0 / p.d_min - 1.0 / p.d_max) / (double)p.num_labels;
+    d.lf = lf;
+    d.L = p.num_labels;
+    d.jitter = p.jitter;
+    d.lf_index = p.lf_index;
+    d.term_mask = (int)p.term_mask;
+    d.iters = p.iterations;
+    d.warm_off = p.warm_iter_offset;
+    d.seed = p.seed;
+    d.inv_dmin = 1.0 / p.d_min;
+    d.inv_dmax = 1.0 / p.d_max;
+    d.delta = (1.0 / p.d_min - 1.0 / p.d_max) / (double)p.num_labels;
     const double unit = fmt == LFD_RGBA8 ? 255.0 : 1.0;
-    c.T = (float)(p.T * unit * unit);
-    c.col_scale = (float)(1.0 / unit);
+    d.T = (float)(p.T * unit * unit);
     const double log2e = 1.4426950408889634;
-    c.k_col = (float)(log2e / (2.0 * p.alpha * p.alpha));
+    d.k_col = (float)(log2e / (2.0 * p.alpha * p.alpha));
     double sigma = p.sigma;
-    if (!(sigma > 0)) sigma = p.depth_domain == 0 ? 2.0 * c.delta : 2.0 * (p.d_max - p.d_min) / p.num_labels;
-    c.k_sig = (float)(log2e / (2.0 * sigma * sigma));
-    c.eta = (float)p.eta;
-    c.xy_lo = (float)(1.0 / (1.0 + p.xy_eps));
-    c.xy_hi = (float)(1.0 + p.xy_eps);
-    return c;
+    if (!(sigma > 0)) sigma = p.depth_domain == 0 ? 2.0 * d.delta : 2.0 * (p.d_max - p.d_min) / p.num_labels;
+    d.k_sig = (float)(log2e / (2.0 * sigma * sigma));
+    d.eta = (float)p.eta;
+    d.xy_lo = (float)(1.0 / (1.0 + p.xy_eps));
+    d.xy_hi = (float)(1.0 + p.xy_eps);
 }
 
 lfd_status ensure_pinned(lfd_ctx *ctx, size_t bytes)
@@ -362,26 +371,32 @@ cudaError_t traced(lfd_ctx *ctx, int stage, cudaStream_t st, F launch)
 }
 
 // -- layout + workspace allocation -------------------------------------------
-lfd_status plan_workspace(lfd_ctx *ctx, const lfd_lightfield *lf)
+constexpr int ORDER_BUCKETS_HOST = 1024;
+
+lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
 {
     Layout L;
-    L.V = lf->num_views;
-    for (int v = 0; v < L.V; v++) {
-        const lfd_camera &c = lf->cams[v];
-        L.W.push_back(c.width);
-        L.H.push_back(c.height);
-        L.GW.push_back(lf->grid_w[v]);
-        L.GH.push_back(lf->grid_h[v]);
-        L.S.push_back(lf->grid_w[v] * lf->grid_h[v]);
-        L.sp_base.push_back(L.S_total);
-        L.px_base.push_back(L.px_total);
-        L.S_total += L.S.back();
-        L.px_total += (long long)c.width * c.height;
-        L.max_px = std::max(L.max_px, c.width * c.height);
-    }
+    for (int l = 0; l < n; l++)
+        for (int v = 0; v < lfs[l].num_views; v++) {
+            const lfd_camera &c = lfs[l].cams[v];
+            L.W.push_back(c.width);
+            L.H.push_back(c.height);
+            L.GW.push_back(lfs[l].grid_w[v]);
+            L.GH.push_back(lfs[l].grid_h[v]);
+            L.S.push_back(lfs[l].grid_w[v] * lfs[l].grid_h[v]);
+            L.sp_base.push_back(L.S_total);
+            L.px_base.push_back(L.px_total);
+            if ((long long)L.S_total + L.S.back() >= (1LL << 30))
+                return fail(ctx, LFD_ERR_INVALID_ARG, "more than 2^30 superpixels in one call");
+            L.S_total += L.S.back();
+            L.px_total += (long long)c.width * c.height;
+            L.max_px = std::max(L.max_px, c.width * c.height);
+            L.V++;
+        }
+    if (L.px_total >= (1LL << 31)) return fail(ctx, LFD_ERR_INVALID_ARG, "more than 2^31 pixels in one call");
     const int V = L.V;
     const size_t S = L.S_total, P = (size_t)L.px_total;
-    const int qb = quad_bytes(lf->fmt);
+    const int qb = quad_bytes(lfs[0].fmt);
     size_t need = 0;
     auto add = [&](size_t b) { need = align_up(need, 256) + b; };
     add(sizeof(ViewDev) * V);
@@ -391,6 +406,7 @@ lfd_status plan_workspace(lfd_ctx *ctx, const lfd_lightfield *lf)
     add(4 * S); add(4 * (S + 1)); add(4 * S); add(4 * P);
     add(8 * S); add(16 * S); add(16 * S); add(32 * S); add(16 * S); add(16 * S);
     add(sizeof(DevCounters));
+    add(4 * S); add(4 * ORDER_BUCKETS_HOST); add(16); add(sizeof(float *) * V);
     add(16 * S); add(16 * S); add(4 * S); add(8 * S); add(8 * S);
     for (int v = 0; v < V; v++) add((size_t)qb * L.W[v] * L.H[v]);
     for (int v = 0; v < V; v++) add((size_t)16 * L.W[v] * L.H[v]);
@@ -413,6 +429,11 @@ lfd_status plan_workspace(lfd_ctx *ctx, const lfd_lightfield *lf)
         }
         ctx->ws.base = (char *)b;
         ctx->ws.cap = need;
+        if (ctx->gexec) {                       // a captured graph points into the old arena
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+            ctx->gsig = 0;
+        }
     }
     Arena &a = ctx->ws;
     a.used = 0;
@@ -432,6 +453,10 @@ lfd_status plan_workspace(lfd_ctx *ctx, const lfd_lightfield *lf)
     ctx->d_sp_rc = (float4 *)a.take(16 * S);
     ctx->d_bbox = (int4 *)a.take(16 * S);
     ctx->d_ctr = (DevCounters *)a.take(sizeof(DevCounters));
+    ctx->d_order = (int *)a.take(4 * S);
+    ctx->d_hist = (int *)a.take(4 * ORDER_BUCKETS_HOST);
+    ctx->d_queue = (int *)a.take(16);
+    ctx->d_depth_ptrs = (float **)a.take(sizeof(float *) * V);
     ctx->d_planesA = (float4 *)a.take(16 * S);
     ctx->d_planesB = (float4 *)a.take(16 * S);
     ctx->d_label = (int *)a.take(4 * S);
@@ -457,6 +482,8 @@ lfd_status plan_workspace(lfd_ctx *ctx, const lfd_lightfield *lf)
     w.radii = ctx->d_radii;
     w.radii_cnt = ctx->d_radii_cnt;
     w.ctr = ctx->d_ctr;
+    w.order = ctx->d_order;
+    w.queue = ctx->d_queue;
     w.S_total = L.S_total;
     w.px_total = L.px_total;
     return LFD_OK;
@@ -468,27 +495,44 @@ __global__ void k_fill_sp_view(int *sp_view, int base, int S, int v)
     if (i < S) sp_view[base + i] = v;
 }
 
-lfd_status set_input_impl(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_params *p, cudaStream_t st)
+// Host half of binding n light fields: validation, workspace, records staged in
+// pinned memory.  Nothing is enqueued.
+lfd_status plan_input(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, const lfd_params *ps, bool host_mem)
 {
     lfd_status s;
-    if ((s = check_params(ctx, p)) != LFD_OK) return s;
-    if ((s = check_lightfield(ctx, lf, false)) != LFD_OK) return s;
-    if ((s = plan_workspace(ctx, lf)) != LFD_OK) return s;
+    if (n < 1 || !lfs || !ps) return fail(ctx, LFD_ERR_INVALID_ARG, "need at least one light field and its parameters");
+    for (int l = 0; l < n; l++) {
+        if ((s = check_params(ctx, &ps[l])) != LFD_OK) return s;
+        if ((s = check_lightfield(ctx, &lfs[l], host_mem)) != LFD_OK) return s;
+        if (lfs[l].fmt != lfs[0].fmt || ps[l].depth_domain != ps[0].depth_domain ||
+            ps[l].sweep_frame != ps[0].sweep_frame)
+            return fail(ctx, LFD_ERR_INVALID_ARG, "light fields of one call must share pixel format, depth domain "
+                                                  "and sweep frame (light field %d differs)", l);
+    }
+    if ((s = plan_workspace(ctx, n, lfs)) != LFD_OK) return s;
     const Layout &L = ctx->L;
     const int V = L.V;
-    ctx->p = *p;
-    ctx->fmt = lf->fmt;
-    ctx->cams.assign(lf->cams, lf->cams + V);
-    ctx->nnb = std::min(V - 1, p->max_neighbor_views > 0 ? p->max_neighbor_views : LFD_MAXN);
-    neighbour_views(lf->cams, V, ctx->nnb, ctx->nbr);
-    ctx->c = make_consts(*p, V, lf->fmt);
+    ctx->fmt = lfs[0].fmt;
+    ctx->lfs.clear();
+    ctx->nbr.assign((size_t)V * LFD_MAXN, -1);
+    Consts c{};
+    c.V = V;
+    c.L = ps[0].num_labels;
+    c.fmt = lfs[0].fmt;
+    c.domain = ps[0].depth_domain;
+    c.sweep_frame = ps[0].sweep_frame;
+    c.col_scale = (float)(lfs[0].fmt == LFD_RGBA8 ? 1.0 / 255.0 : 1.0);
+    ctx->c = c;
 
-    // host records -> pinned staging -> device
     const size_t bytes_views = sizeof(ViewDev) * V, bytes_pairs = sizeof(PairDev) * V * LFD_MAXN;
     const size_t bytes_radii = 2 * (size_t)V * (LFD_MAX_ITER_INDEX + 1) * LFD_MAX_RADII;
     const size_t bytes_rcnt = 4 * (size_t)V * (LFD_MAX_ITER_INDEX + 1);
     const size_t o_pairs = align_up(bytes_views, 256), o_radii = align_up(o_pairs + bytes_pairs, 256),
                  o_rcnt = align_up(o_radii + bytes_radii, 256), total = o_rcnt + bytes_rcnt;
+    if ((char *)ctx->d_pairs - (char *)ctx->d_views != (ptrdiff_t)o_pairs ||
+        (char *)ctx->d_radii - (char *)ctx->d_views != (ptrdiff_t)o_radii ||
+        (char *)ctx->d_radii_cnt - (char *)ctx->d_views != (ptrdiff_t)o_rcnt)
+        return fail(ctx, LFD_ERR_STATE, "internal: workspace record layout mismatch");
     if ((s = ensure_pinned(ctx, total)) != LFD_OK) return s;
     char *h = (char *)ctx->h_stage;
     memset(h, 0, total);
@@ -496,70 +540,93 @@ lfd_status set_input_impl(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_para
     PairDev *hp = (PairDev *)(h + o_pairs);
     short *hr = (short *)(h + o_radii);
     int *hrc = (int *)(h + o_rcnt);
-    std::vector<std::vector<double>> Kinv(V, std::vector<double>(9));
-    for (int v = 0; v < V; v++) inv_pinhole(lf->cams[v].K, Kinv[v].data());
-    for (int v = 0; v < V; v++) {
-        const lfd_camera &cv = lf->cams[v];
-        ViewDev &d = hv[v];
-        d.W = L.W[v]; d.H = L.H[v]; d.GW = L.GW[v]; d.GH = L.GH[v];
-        d.S = L.S[v]; d.sp_base = L.sp_base[v]; d.px_base = L.px_base[v];
-        d.nnb = ctx->nnb;
-        memcpy(d.Kinv, Kinv[v].data(), sizeof(d.Kinv));
-        for (int k = 0; k < 3; k++) d.wz[k] = cv.R[3 * k + 2];
-        d.labels = lf->labels[v];
-        d.quad = ctx->quads[v];
-        d.map = ctx->maps[v];
-        // propagation kernel: Size_init in cells (Section IV-A: smallest image dimension by default)
-        const double pitch = std::sqrt((double)d.W * d.H / ((double)d.GW * d.GH));
-        const int size_px = p->kernel_size_init > 0 ? p->kernel_size_init : std::min(d.W, d.H);
-        d.ksize_init = (int)std::floor((double)size_px / pitch);
-        d.ksteps_init = (int)std::floor((double)d.ksize_init / p->kernel_step_sp + 0.5);
-        for (int I = 0; I <= LFD_MAX_ITER_INDEX; I++) {
-            const int n = kernel_radii(d.ksize_init, d.ksteps_init, I, nullptr, 0);
-            if (n > LFD_MAX_RADII)
-                return fail(ctx, LFD_ERR_INVALID_ARG, "propagation kernel of iteration %d has %d radii (max %d); "
-                            "raise kernel_step_sp", I, n, LFD_MAX_RADII);
-            int rr[LFD_MAX_RADII];
-            kernel_radii(d.ksize_init, d.ksteps_init, I, rr, LFD_MAX_RADII);
-            hrc[v * (LFD_MAX_ITER_INDEX + 1) + I] = n;
-            for (int k = 0; k < n; k++) hr[((size_t)v * (LFD_MAX_ITER_INDEX + 1) + I) * LFD_MAX_RADII + k] = (short)rr[k];
-        }
-        for (int k = 0; k < ctx->nnb; k++) {
-            const int i = ctx->nbr[(size_t)v * LFD_MAXN + k];
-            const lfd_camera &ci = lf->cams[i];
-            // R_rel = R_i R_v^T, t_rel = t_i - R_rel t_v, P = K_i R_rel K_v^-1, q = K_i t_rel
-            double Rrel[9], tmp[9], P[9];
-            for (int r = 0; r < 3; r++)
-                for (int cc = 0; cc < 3; cc++)
-                    Rrel[3 * r + cc] = ci.R[3 * r] * cv.R[3 * cc] + ci.R[3 * r + 1] * cv.R[3 * cc + 1] +
-                                       ci.R[3 * r + 2] * cv.R[3 * cc + 2];
-            double trel[3];
-            for (int r = 0; r < 3; r++)
-                trel[r] = ci.t[r] - (Rrel[3 * r] * cv.t[0] + Rrel[3 * r + 1] * cv.t[1] + Rrel[3 * r + 2] * cv.t[2]);
-            mat_mul(ci.K, Rrel, tmp);
-            mat_mul(tmp, Kinv[v].data(), P);
-            PairDev &pd = hp[v * LFD_MAXN + k];
-            pd.i = i;
-            pd.Wi = L.W[i];
-            pd.Hi = L.H[i];
-            for (int r = 0; r < 9; r++) {
-                pd.P[r] = P[r];
-                pd.Pf[r] = (float)P[r];
+    const int tb = texel_bytes(lfs[0].fmt);
+    int gv = 0;
+    for (int l = 0; l < n; l++) {
+        const lfd_lightfield &lf = lfs[l];
+        const lfd_params &p = ps[l];
+        ctx->lfs.push_back({gv, lf.num_views, p});
+        const int nnb = std::min(lf.num_views - 1, p.max_neighbor_views > 0 ? p.max_neighbor_views : LFD_MAXN);
+        std::vector<int> nb;
+        neighbour_views(lf.cams, lf.num_views, nnb, nb);
+        std::vector<std::vector<double>> Kinv(lf.num_views, std::vector<double>(9));
+        for (int v = 0; v < lf.num_views; v++) inv_pinhole(lf.cams[v].K, Kinv[v].data());
+        for (int v = 0; v < lf.num_views; v++, gv++) {
+            const lfd_camera &cv = lf.cams[v];
+            ViewDev &d = hv[gv];
+            d.W = L.W[gv]; d.H = L.H[gv]; d.GW = L.GW[gv]; d.GH = L.GH[gv];
+            d.S = L.S[gv]; d.sp_base = L.sp_base[gv]; d.px_base = L.px_base[gv];
+            d.nnb = nnb;
+            memcpy(d.Kinv, Kinv[v].data(), sizeof(d.Kinv));
+            for (int k = 0; k < 3; k++) d.wz[k] = cv.R[3 * k + 2];
+            d.labels = lf.labels[v];
+            d.img = lf.views[v];
+            d.pitch = (lf.view_pitch_bytes && lf.view_pitch_bytes[v]) ? lf.view_pitch_bytes[v] : (long long)d.W * tb;
+            d.quad = ctx->quads[gv];
+            d.map = ctx->maps[gv];
+            view_params(d, p, lf.fmt, l);
+            d.lv = v;
+            // propagation kernel: Size_init in cells (Section IV-A: smallest image dimension by default)
+            const double pitch = std::sqrt((double)d.W * d.H / ((double)d.GW * d.GH));
+            const int size_px = p.kernel_size_init > 0 ? p.kernel_size_init : std::min(d.W, d.H);
+            d.ksize_init = (int)std::floor((double)size_px / pitch);
+            d.ksteps_init = (int)std::floor((double)d.ksize_init / p.kernel_step_sp + 0.5);
+            for (int I = 0; I <= LFD_MAX_ITER_INDEX; I++) {
+                const int nr = kernel_radii(d.ksize_init, d.ksteps_init, I, nullptr, 0);
+                if (nr > LFD_MAX_RADII)
+                    return fail(ctx, LFD_ERR_INVALID_ARG, "propagation kernel of iteration %d has %d radii (max %d); "
+                                "raise kernel_step_sp", I, nr, LFD_MAX_RADII);
+                int rr[LFD_MAX_RADII];
+                kernel_radii(d.ksize_init, d.ksteps_init, I, rr, LFD_MAX_RADII);
+                hrc[gv * (LFD_MAX_ITER_INDEX + 1) + I] = nr;
+                for (int k = 0; k < nr; k++)
+                    hr[((size_t)gv * (LFD_MAX_ITER_INDEX + 1) + I) * LFD_MAX_RADII + k] = (short)rr[k];
             }
-            for (int r = 0; r < 3; r++) {
-                pd.q[r] = ci.K[3 * r] * trel[0] + ci.K[3 * r + 1] * trel[1] + ci.K[3 * r + 2] * trel[2];
-                pd.qf[r] = (float)pd.q[r];
+            for (int k = 0; k < nnb; k++) {
+                const int i = nb[(size_t)v * LFD_MAXN + k];
+                const int gi = ctx->lfs[l].first_view + i;
+                ctx->nbr[(size_t)gv * LFD_MAXN + k] = gi;
+                const lfd_camera &ci = lf.cams[i];
+                // R_rel = R_i R_v^T, t_rel = t_i - R_rel t_v, P = K_i R_rel K_v^-1, q = K_i t_rel
+                double Rrel[9], tmp[9], P[9];
+                for (int r = 0; r < 3; r++)
+                    for (int cc = 0; cc < 3; cc++)
+                        Rrel[3 * r + cc] = ci.R[3 * r] * cv.R[3 * cc] + ci.R[3 * r + 1] * cv.R[3 * cc + 1] +
+                                           ci.R[3 * r + 2] * cv.R[3 * cc + 2];
+                double trel[3];
+                for (int r = 0; r < 3; r++)
+                    trel[r] = ci.t[r] - (Rrel[3 * r] * cv.t[0] + Rrel[3 * r + 1] * cv.t[1] + Rrel[3 * r + 2] * cv.t[2]);
+                mat_mul(ci.K, Rrel, tmp);
+                mat_mul(tmp, Kinv[v].data(), P);
+                PairDev &pd = hp[gv * LFD_MAXN + k];
+                pd.i = gi;
+                pd.Wi = L.W[gi];
+                pd.Hi = L.H[gi];
+                for (int r = 0; r < 9; r++) {
+                    pd.P[r] = P[r];
+                    pd.Pf[r] = (float)P[r];
+                }
+                for (int r = 0; r < 3; r++) {
+                    pd.q[r] = ci.K[3 * r] * trel[0] + ci.K[3 * r + 1] * trel[1] + ci.K[3 * r + 2] * trel[2];
+                    pd.qf[r] = (float)pd.q[r];
+                }
+                pd.quad_i = ctx->quads[gi];
+                pd.map_i = ctx->maps[gi];
             }
-            pd.quad_i = ctx->quads[i];
-            pd.map_i = ctx->maps[i];
         }
     }
-    if ((char *)ctx->d_pairs - (char *)ctx->d_views != (ptrdiff_t)o_pairs ||
-        (char *)ctx->d_radii - (char *)ctx->d_views != (ptrdiff_t)o_radii ||
-        (char *)ctx->d_radii_cnt - (char *)ctx->d_views != (ptrdiff_t)o_rcnt)
-        return fail(ctx, LFD_ERR_STATE, "internal: workspace record layout mismatch");
-    LFD_CUDA(cudaMemcpyAsync(ctx->d_views, h, total, cudaMemcpyHostToDevice, st));
-    LFD_CUDA(cudaEventRecord(ctx->ev_stage, st));
+    return LFD_OK;
+}
+
+// Device half: upload the staged records and build superpixels, textures and
+// the cost order.  Capturable (no allocation, no synchronisation).
+lfd_status enqueue_input(lfd_ctx *ctx, cudaStream_t st, bool record_event)
+{
+    const Layout &L = ctx->L;
+    const int V = L.V;
+    const size_t total = (char *)(ctx->d_radii_cnt + (size_t)V * (LFD_MAX_ITER_INDEX + 1)) - (char *)ctx->d_views;
+    LFD_CUDA(cudaMemcpyAsync(ctx->d_views, ctx->h_stage, total, cudaMemcpyHostToDevice, st));
+    if (record_event) LFD_CUDA(cudaEventRecord(ctx->ev_stage, st));
     LFD_CUDA(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
     for (int v = 0; v < V; v++) {
         LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
@@ -567,26 +634,34 @@ lfd_status set_input_impl(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_para
             return cudaGetLastError();
         }));
     }
-
-    ViewPtrs img;
-    memset(&img, 0, sizeof(img));
-    const int tb = texel_bytes(lf->fmt);
-    for (int v = 0; v < V; v++) {
-        img.p[v] = lf->views[v];
-        img.pitch[v] = (lf->view_pitch_bytes && lf->view_pitch_bytes[v]) ? lf->view_pitch_bytes[v] : (long long)L.W[v] * tb;
-    }
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
         return launch_sp_count(ctx->w, V, L.max_px, ctx->d_sp_cnt, ctx->d_bbox, st);
     }));
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st,
                     [&] { return launch_sp_scan(ctx->w, V, ctx->d_sp_cnt, ctx->d_sp_off, st); }));
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
-        return launch_sp_collect(ctx->w, ctx->c, img, ctx->d_bbox, ctx->d_sp_cnt, ctx->d_sp_pix, ctx->d_sp_cen,
+        return launch_sp_collect(ctx->w, ctx->c, ctx->d_bbox, ctx->d_sp_cnt, ctx->d_sp_pix, ctx->d_sp_cen,
                                  ctx->d_sp_ref, ctx->d_sp_col, st);
     }));
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_sp_minw(ctx->w, ctx->c, ctx->d_sp_col, st); }));
-    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st,
-                    [&] { return launch_quads(ctx->w, V, L.max_px, lf->fmt, img, st); }));
+    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_quads(ctx->w, V, L.max_px, ctx->fmt, st); }));
+    if (ctx->lc.sweep_persistent || ctx->lc.prop_persistent)
+        LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st,
+                        [&] { return launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, st); }));
+    return LFD_OK;
+}
+
+lfd_status set_input_multi(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, const lfd_params *ps, cudaStream_t st)
+{
+    lfd_status s;
+    ctx->bound = false;
+    if (ctx->gexec) {               // the staging a captured graph reads is about to change
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+        ctx->gsig = 0;
+    }
+    if ((s = plan_input(ctx, n, lfs, ps, false)) != LFD_OK) return s;
+    if ((s = enqueue_input(ctx, st, true)) != LFD_OK) return s;
     ctx->bound = true;
     return LFD_OK;
 }
@@ -610,57 +685,240 @@ lfd_status gather_planes(lfd_ctx *ctx, const float *const *src, float4 *dst, cud
 
 template <typename T>
 lfd_status scatter(lfd_ctx *ctx, const T *src, T *const *dst, size_t per_sp, cudaStream_t st,
-                   cudaMemcpyKind kind = cudaMemcpyDeviceToDevice)
+                   cudaMemcpyKind kind = cudaMemcpyDeviceToDevice, int first_view = 0, int nviews = -1)
 {
     if (!dst) return LFD_OK;
-    for (int v = 0; v < ctx->L.V; v++) {
-        if (!dst[v]) continue;
-        LFD_CUDA(cudaMemcpyAsync(dst[v], src + (size_t)ctx->L.sp_base[v] * per_sp, sizeof(T) * per_sp * ctx->L.S[v],
+    if (nviews < 0) nviews = ctx->L.V;
+    for (int k = 0; k < nviews; k++) {
+        const int v = first_view + k;
+        if (!dst[k]) continue;
+        LFD_CUDA(cudaMemcpyAsync(dst[k], src + (size_t)ctx->L.sp_base[v] * per_sp, sizeof(T) * per_sp * ctx->L.S[v],
                                  kind, st));
     }
     return LFD_OK;
 }
 
-lfd_status rasterize_state(lfd_ctx *ctx, const float4 *planes, const OutPtrs *depth, cudaStream_t st)
+// Upload a per-view table of depth-output pointers (NULL entries allowed).
+lfd_status upload_depth_ptrs(lfd_ctx *ctx, float *const *per_view, cudaStream_t st, float ***dev_out)
 {
-    LFD_CUDA(traced(ctx, LFD_STAGE_RASTER, st,
-                    [&] { return launch_plane_prep(ctx->w, ctx->c, planes, ctx->d_sp_g, ctx->d_sp_rc, st); }));
-    LFD_CUDA(traced(ctx, LFD_STAGE_RASTER, st, [&] { return launch_rasterize(ctx->w, ctx->c, depth, st); }));
+    *dev_out = nullptr;
+    if (!per_view) return LFD_OK;
+    const int V = ctx->L.V;
+    if (ctx->ev_depth) LFD_CUDA(cudaEventSynchronize(ctx->ev_depth));
+    if (ctx->h_depth_cap < V) {
+        if (ctx->h_depth) cudaFreeHost(ctx->h_depth);
+        ctx->h_depth = nullptr;
+        ctx->h_depth_cap = 0;
+        LFD_CUDA(cudaMallocHost(&ctx->h_depth, sizeof(float *) * V));
+        ctx->h_depth_cap = V;
+    }
+    for (int v = 0; v < V; v++) ctx->h_depth[v] = per_view[v];
+    LFD_CUDA(cudaMemcpyAsync(ctx->d_depth_ptrs, ctx->h_depth, sizeof(float *) * V, cudaMemcpyHostToDevice, st));
+    LFD_CUDA(cudaEventRecord(ctx->ev_depth, st));
+    *dev_out = ctx->d_depth_ptrs;
     return LFD_OK;
 }
 
-lfd_status iterate_flat(lfd_ctx *ctx, int iter, const float4 *in, float4 *out, int *choice, float *energy, cudaStream_t st)
+lfd_status rasterize_state(lfd_ctx *ctx, const float4 *planes, float *const *depth_dev, cudaStream_t st)
 {
-    lfd_status s;
-    if ((s = rasterize_state(ctx, in, nullptr, st)) != LFD_OK) return s;
-    LFD_CUDA(traced(ctx, LFD_STAGE_PROPAGATE, st, [&] {
-        return launch_propagate(ctx->w, ctx->c, iter + ctx->p.warm_iter_offset, in, out, choice, energy, st);
+    LFD_CUDA(traced(ctx, LFD_STAGE_RASTER, st,
+                    [&] { return launch_plane_prep(ctx->w, ctx->c, planes, ctx->d_sp_g, ctx->d_sp_rc, st); }));
+    LFD_CUDA(traced(ctx, LFD_STAGE_RASTER, st, [&] { return launch_rasterize(ctx->w, ctx->c, depth_dev, st); }));
+    return LFD_OK;
+}
+
+lfd_status run_sweep(lfd_ctx *ctx, float *cost, cudaStream_t st)
+{
+    if (ctx->lc.sweep_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 16, st));
+    LFD_CUDA(traced(ctx, LFD_STAGE_SWEEP, st, [&] {
+        return launch_sweep(ctx->w, ctx->c, ctx->lc, ctx->d_planesA, ctx->d_label, cost, st);
     }));
     return LFD_OK;
 }
 
-lfd_status estimate_impl(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_params *p, const float *const *warm,
-                         float *const *planes_out, const OutPtrs *depth, cudaStream_t st, bool planes_to_host)
+// One iteration over every bound view.  In a frame (`frame`), a view whose
+// light field has already run its own iteration count passes its plane through.
+lfd_status iterate_flat(lfd_ctx *ctx, int iter, const float4 *in, float4 *out, int *choice, float *energy,
+                        cudaStream_t st, bool frame = false)
 {
     lfd_status s;
-    if ((s = set_input_impl(ctx, lf, p, st)) != LFD_OK) return s;
+    if ((s = rasterize_state(ctx, in, nullptr, st)) != LFD_OK) return s;
+    if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 16, st));
+    Consts c = ctx->c;
+    c.batch_iters = frame ? 1 : 0;
+    LFD_CUDA(traced(ctx, LFD_STAGE_PROPAGATE, st, [&] {
+        return launch_propagate(ctx->w, c, ctx->lc, iter, in, out, choice, energy, st);
+    }));
+    return LFD_OK;
+}
+
+int max_iterations(const lfd_ctx *ctx)
+{
+    int m = 0;
+    for (const LfInfo &l : ctx->lfs) m = std::max(m, l.p.iterations);
+    return m;
+}
+
+// The device work of one frame after the inputs are bound: sweep (or warm
+// planes), all iterations, final rasterisation, planes out.  Capturable.
+lfd_status enqueue_frame(lfd_ctx *ctx, const float *const *warm, float *const *const *planes_out,
+                         float *const *depth_dev, cudaStream_t st, cudaMemcpyKind out_kind)
+{
+    lfd_status s;
     if (warm) {
         if ((s = gather_planes(ctx, warm, ctx->d_planesA, st)) != LFD_OK) return s;
     } else {
-        LFD_CUDA(traced(ctx, LFD_STAGE_SWEEP, st,
-                        [&] { return launch_sweep(ctx->w, ctx->c, ctx->d_planesA, ctx->d_label, nullptr, st); }));
+        if ((s = run_sweep(ctx, nullptr, st)) != LFD_OK) return s;
     }
     float4 *a = ctx->d_planesA, *b = ctx->d_planesB;
-    for (int it = 1; it <= p->iterations; it++) {
-        if ((s = iterate_flat(ctx, it, a, b, nullptr, nullptr, st)) != LFD_OK) return s;
+    const int iters = max_iterations(ctx);
+    for (int it = 1; it <= iters; it++) {
+        if ((s = iterate_flat(ctx, it, a, b, nullptr, nullptr, st, true)) != LFD_OK) return s;
         std::swap(a, b);
     }
-    if ((s = rasterize_state(ctx, a, depth, st)) != LFD_OK) return s;
-    if (planes_out) {
-        if ((s = scatter<float>(ctx, (const float *)a, planes_out, 4, st,
-                                planes_to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice)) != LFD_OK)
-            return s;
+    if ((s = rasterize_state(ctx, a, depth_dev, st)) != LFD_OK) return s;
+    if (planes_out)
+        for (size_t l = 0; l < ctx->lfs.size(); l++)
+            if ((s = scatter<float>(ctx, (const float *)a, planes_out[l], 4, st, out_kind, ctx->lfs[l].first_view,
+                                    ctx->lfs[l].V)) != LFD_OK)
+                return s;
+    return LFD_OK;
+}
+
+// Launch-shape autotuner: times each sweep and propagate variant on the bound
+// input (one warm-up run, then the median of three) and keeps the fastest.
+lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
+{
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    cudaEvent_t e0, e1;
+    LFD_CUDA(cudaEventCreate(&e0));
+    LFD_CUDA(cudaEventCreate(&e1));
+    auto time_it = [&](auto &&fn, float &ms) -> lfd_status {
+        lfd_status s;
+        float t[3];
+        if ((s = fn()) != LFD_OK) return s;
+        for (int r = 0; r < 3; r++) {
+            LFD_CUDA(cudaEventRecord(e0, st));
+            if ((s = fn()) != LFD_OK) return s;
+            LFD_CUDA(cudaEventRecord(e1, st));
+            LFD_CUDA(cudaEventSynchronize(e1));
+            LFD_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
+        }
+        std::sort(t, t + 3);
+        ms = t[1];
+        return LFD_OK;
+    };
+    lfd_status s;
+    LaunchCfg best = ctx->lc;
+    // superpixel cost order for the persistent variants
+    LFD_CUDA(launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, st));
+    float best_ms = 1e30f;
+    const int th[2] = {128, 256};
+    for (int pi = 0; pi < 2; pi++)
+        for (int ti = 0; ti < 2; ti++) {
+            ctx->lc.sweep_threads = th[ti];
+            ctx->lc.sweep_persistent = pi;
+            float ms = 0;
+            if ((s = time_it([&] { return run_sweep(ctx, nullptr, st); }, ms)) != LFD_OK) return s;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.sweep_threads = th[ti];
+                best.sweep_persistent = pi;
+            }
+        }
+    ctx->lc.sweep_threads = best.sweep_threads;
+    ctx->lc.sweep_persistent = best.sweep_persistent;
+    if ((s = run_sweep(ctx, nullptr, st)) != LFD_OK) return s;
+    if ((s = rasterize_state(ctx, ctx->d_planesA, nullptr, st)) != LFD_OK) return s;
+    best_ms = 1e30f;
+    const int pb[2] = {7, 8};
+    for (int pi = 0; pi < 2; pi++)
+        for (int bi = 0; bi < 2; bi++) {
+            ctx->lc.prop_blocks = pb[bi];
+            ctx->lc.prop_persistent = pi;
+            float ms = 0;
+            auto fn = [&]() -> lfd_status {
+                if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 16, st));
+                LFD_CUDA(launch_propagate(ctx->w, ctx->c, ctx->lc, 1, ctx->d_planesA, ctx->d_planesB, nullptr, nullptr,
+                                          st));
+                return LFD_OK;
+            };
+            if ((s = time_it(fn, ms)) != LFD_OK) return s;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.prop_blocks = pb[bi];
+                best.prop_persistent = pi;
+            }
+        }
+    ctx->lc = best;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->prof = prof;
+    return LFD_OK;
+}
+
+uint64_t mix64(uint64_t h, uint64_t v)
+{
+    h ^= v + 0x9E3779B97F4A7C15ULL + (h << 6) + (h >> 2);
+    return h;
+}
+
+uint64_t hash_bytes(uint64_t h, const void *p, size_t n)
+{
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < n; i++) h = mix64(h, b[i]);
+    return h;
+}
+
+// signature of a batched call: every pointer, size, camera and parameter
+uint64_t batch_signature(int n, const lfd_lightfield *lfs, const lfd_params *ps, float *const *const *planes_out,
+                         float *const *const *depth_out, const lfd_batch_options *opt)
+{
+    uint64_t h = mix64(0x1234, (uint64_t)n);
+    for (int l = 0; l < n; l++) {
+        const lfd_lightfield &lf = lfs[l];
+        h = mix64(h, (uint64_t)lf.num_views);
+        h = mix64(h, (uint64_t)lf.fmt);
+        h = hash_bytes(h, &ps[l], sizeof(lfd_params));
+        for (int v = 0; v < lf.num_views; v++) {
+            h = hash_bytes(h, &lf.cams[v], sizeof(lfd_camera));
+            h = mix64(h, (uint64_t)(uintptr_t)lf.views[v]);
+            h = mix64(h, (uint64_t)(uintptr_t)lf.labels[v]);
+            h = mix64(h, (uint64_t)(lf.view_pitch_bytes ? lf.view_pitch_bytes[v] : 0));
+            h = mix64(h, (uint64_t)lf.grid_w[v] * 65536u + (uint64_t)lf.grid_h[v]);
+            h = mix64(h, (uint64_t)(uintptr_t)(planes_out && planes_out[l] ? planes_out[l][v] : nullptr));
+            h = mix64(h, (uint64_t)(uintptr_t)(depth_out && depth_out[l] ? depth_out[l][v] : nullptr));
+        }
     }
+    h = hash_bytes(h, opt, sizeof(*opt));
+    return h | 1;
+}
+
+}  // namespace
+
+namespace {
+
+void drop_graph(lfd_ctx *ctx)
+{
+    if (!ctx->gexec) return;
+    if (ctx->ev_stage) cudaEventSynchronize(ctx->ev_stage);   // the last replay has finished
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+    ctx->gsig = 0;
+}
+
+lfd_status apply_options(lfd_ctx *ctx, const lfd_batch_options &o)
+{
+    if ((o.sweep_threads != 0 && o.sweep_threads != 128 && o.sweep_threads != 256) ||
+        (o.prop_blocks != 0 && o.prop_blocks != 7 && o.prop_blocks != 8) || (o.sweep_persistent & ~1) ||
+        (o.prop_persistent & ~1) || (o.autotune & ~1) || (o.graph & ~1))
+        return fail(ctx, LFD_ERR_INVALID_ARG, "batch options: sweep_threads 0/128/256, prop_blocks 0/7/8, flags 0/1");
+    if (o.autotune) return LFD_OK;
+    ctx->lc.sweep_threads = o.sweep_threads ? o.sweep_threads : 256;
+    ctx->lc.sweep_persistent = o.sweep_persistent;
+    ctx->lc.prop_blocks = o.prop_blocks ? o.prop_blocks : 7;
+    ctx->lc.prop_persistent = o.prop_persistent;
     return LFD_OK;
 }
 
@@ -681,6 +939,7 @@ void lfd_struct_sizes(int32_t *out)
     out[1] = (int32_t)sizeof(lfd_lightfield);
     out[2] = (int32_t)sizeof(lfd_params);
     out[3] = (int32_t)sizeof(lfd_query);
+    out[4] = (int32_t)sizeof(lfd_batch_options);
 }
 
 const char *lfd_status_string(lfd_status s)
@@ -724,6 +983,14 @@ void lfd_params_default(lfd_params *p)
     p->warm_iter_offset = 0;
 }
 
+void lfd_batch_options_default(lfd_batch_options *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->sweep_threads = 256;
+    o->prop_blocks = 7;
+}
+
 lfd_status lfd_create(lfd_ctx **out, int32_t device, uint64_t hbm_budget_bytes)
 {
     if (!out) return LFD_ERR_INVALID_ARG;
@@ -737,11 +1004,18 @@ lfd_status lfd_create(lfd_ctx **out, int32_t device, uint64_t hbm_budget_bytes)
     if (!ctx) return LFD_ERR_OOM;
     ctx->device = device;
     ctx->budget = hbm_budget_bytes;
-    if (cudaSetDevice(device) != cudaSuccess || cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_depth, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_bdepth, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        if (ctx->ev_stage) cudaEventDestroy(ctx->ev_stage);
+        if (ctx->ev_depth) cudaEventDestroy(ctx->ev_depth);
         delete ctx;
         return LFD_ERR_CUDA;
     }
+    ctx->lc.num_sms = ctx->num_sms;
     *out = ctx;
     return LFD_OK;
 }
@@ -751,6 +1025,7 @@ lfd_status lfd_destroy(lfd_ctx *ctx)
     if (!ctx) return LFD_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->ws.base) cudaFree(ctx->ws.base);
     if (ctx->d_cost) cudaFree(ctx->d_cost);
     if (ctx->d_stage_in) cudaFree(ctx->d_stage_in);
@@ -758,7 +1033,11 @@ lfd_status lfd_destroy(lfd_ctx *ctx)
     if (ctx->d_q) cudaFree(ctx->d_q);
     if (ctx->d_qout) cudaFree(ctx->d_qout);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->h_depth) cudaFreeHost(ctx->h_depth);
+    if (ctx->h_bdepth) cudaFreeHost(ctx->h_bdepth);
     if (ctx->ev_stage) cudaEventDestroy(ctx->ev_stage);
+    if (ctx->ev_depth) cudaEventDestroy(ctx->ev_depth);
+    if (ctx->ev_bdepth) cudaEventDestroy(ctx->ev_bdepth);
     for (auto &u : ctx->prof_used) {
         cudaEventDestroy(u.second.first);
         cudaEventDestroy(u.second.second);
@@ -776,8 +1055,8 @@ lfd_status lfd_set_input(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_param
     ctx->err.clear();
     lfd_status s;
     if ((s = set_device(ctx)) != LFD_OK) return s;
-    ctx->bound = false;
-    return set_input_impl(ctx, lf, p, (cudaStream_t)stream);
+    if (!lf || !p) return fail(ctx, LFD_ERR_INVALID_ARG, "light field or params is NULL");
+    return set_input_multi(ctx, 1, lf, p, (cudaStream_t)stream);
 }
 
 lfd_status lfd_num_superpixels(const lfd_ctx *ctx, int32_t view, int32_t *out)
@@ -799,15 +1078,17 @@ lfd_status lfd_plane_sweep(lfd_ctx *ctx, float *const *planes_out, int32_t *cons
     cudaStream_t st = (cudaStream_t)stream;
     float *cost = nullptr;
     if (cost_out) {
-        const size_t need = sizeof(float) * (size_t)ctx->L.S_total * ctx->p.num_labels;
+        for (const LfInfo &l : ctx->lfs)
+            if (l.p.num_labels != ctx->c.L)
+                return fail(ctx, LFD_ERR_INVALID_ARG, "cost_out needs one label count across the bound light fields");
+        const size_t need = sizeof(float) * (size_t)ctx->L.S_total * ctx->c.L;
         if ((s = ensure_dev(ctx, (void **)&ctx->d_cost, &ctx->cost_cap, need)) != LFD_OK) return s;
         cost = ctx->d_cost;
     }
-    LFD_CUDA(traced(ctx, LFD_STAGE_SWEEP, st,
-                    [&] { return launch_sweep(ctx->w, ctx->c, ctx->d_planesA, ctx->d_label, cost, st); }));
+    if ((s = run_sweep(ctx, cost, st)) != LFD_OK) return s;
     if ((s = scatter<float>(ctx, (const float *)ctx->d_planesA, planes_out, 4, st)) != LFD_OK) return s;
     if ((s = scatter<int32_t>(ctx, ctx->d_label, label_out, 1, st)) != LFD_OK) return s;
-    if (cost_out && (s = scatter<float>(ctx, cost, cost_out, ctx->p.num_labels, st)) != LFD_OK) return s;
+    if (cost_out && (s = scatter<float>(ctx, cost, cost_out, ctx->c.L, st)) != LFD_OK) return s;
     return LFD_OK;
 }
 
@@ -818,11 +1099,9 @@ lfd_status lfd_rasterize(lfd_ctx *ctx, const float *const *planes, float *const 
     if ((s = set_device(ctx)) != LFD_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = gather_planes(ctx, planes, ctx->d_planesA, st)) != LFD_OK) return s;
-    OutPtrs dp;
-    memset(&dp, 0, sizeof(dp));
-    if (depth_out)
-        for (int v = 0; v < ctx->L.V; v++) dp.p[v] = depth_out[v];
-    return rasterize_state(ctx, ctx->d_planesA, depth_out ? &dp : nullptr, st);
+    float **dp = nullptr;
+    if ((s = upload_depth_ptrs(ctx, depth_out, st, &dp)) != LFD_OK) return s;
+    return rasterize_state(ctx, ctx->d_planesA, dp, st);
 }
 
 lfd_status lfd_iterate(lfd_ctx *ctx, int32_t iter, const float *const *planes_in, float *const *planes_out,
@@ -831,9 +1110,10 @@ lfd_status lfd_iterate(lfd_ctx *ctx, int32_t iter, const float *const *planes_in
     lfd_status s;
     if ((s = need_bound(ctx)) != LFD_OK) return s;
     if ((s = set_device(ctx)) != LFD_OK) return s;
-    if (iter < 1 || iter + ctx->p.warm_iter_offset > LFD_MAX_ITER_INDEX)
-        return fail(ctx, LFD_ERR_INVALID_ARG, "iteration index %d outside 1..%d", iter,
-                    LFD_MAX_ITER_INDEX - ctx->p.warm_iter_offset);
+    int warm = 0;
+    for (const LfInfo &l : ctx->lfs) warm = std::max(warm, l.p.warm_iter_offset);
+    if (iter < 1 || iter + warm > LFD_MAX_ITER_INDEX)
+        return fail(ctx, LFD_ERR_INVALID_ARG, "iteration index %d outside 1..%d", iter, LFD_MAX_ITER_INDEX - warm);
     if (!planes_out) return fail(ctx, LFD_ERR_INVALID_ARG, "planes_out is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = gather_planes(ctx, planes_in, ctx->d_planesA, st)) != LFD_OK) return s;
@@ -854,11 +1134,13 @@ lfd_status lfd_estimate(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_params
     lfd_status s;
     if ((s = set_device(ctx)) != LFD_OK) return s;
     if (!planes_out) return fail(ctx, LFD_ERR_INVALID_ARG, "planes_out is NULL");
-    OutPtrs dp;
-    memset(&dp, 0, sizeof(dp));
-    if (depth_out && lf && lf->num_views <= LFD_MAX_VIEWS)
-        for (int v = 0; v < lf->num_views; v++) dp.p[v] = depth_out[v];
-    return estimate_impl(ctx, lf, p, warm_planes, planes_out, depth_out ? &dp : nullptr, (cudaStream_t)stream, false);
+    if (!lf || !p) return fail(ctx, LFD_ERR_INVALID_ARG, "light field or params is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = set_input_multi(ctx, 1, lf, p, st)) != LFD_OK) return s;
+    float **dp = nullptr;
+    if ((s = upload_depth_ptrs(ctx, depth_out, st, &dp)) != LFD_OK) return s;
+    float *const *po[1] = {planes_out};
+    return enqueue_frame(ctx, warm_planes, po, dp, st, cudaMemcpyDeviceToDevice);
 }
 
 lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const lfd_params *p,
@@ -884,6 +1166,7 @@ lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const 
         o_dep[v] = need_depth;
         need_depth += npx;
     }
+    drop_graph(ctx);
     if ((s = ensure_dev(ctx, &ctx->d_stage_in, &ctx->stage_in_cap, need_in)) != LFD_OK) return s;
     if (depth_out_host &&
         (s = ensure_dev(ctx, (void **)&ctx->d_stage_depth, &ctx->stage_depth_cap, need_depth * 4)) != LFD_OK)
@@ -908,21 +1191,152 @@ lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const 
     lfd.views = dv.data();
     lfd.labels = dl.data();
     lfd.view_pitch_bytes = pitch.data();
-    OutPtrs dp;
-    memset(&dp, 0, sizeof(dp));
+    std::vector<float *> dptr(V, nullptr);
     if (depth_out_host)
-        for (int v = 0; v < V; v++) dp.p[v] = ctx->d_stage_depth + o_dep[v];
-    if ((s = estimate_impl(ctx, &lfd, p, nullptr, planes_out_host, depth_out_host ? &dp : nullptr, st, true)) != LFD_OK)
-        return s;
+        for (int v = 0; v < V; v++) dptr[v] = ctx->d_stage_depth + o_dep[v];
+    if ((s = set_input_multi(ctx, 1, &lfd, p, st)) != LFD_OK) return s;
+    float **dp = nullptr;
+    if ((s = upload_depth_ptrs(ctx, depth_out_host ? dptr.data() : nullptr, st, &dp)) != LFD_OK) return s;
+    float *const *po[1] = {planes_out_host};
+    if ((s = enqueue_frame(ctx, nullptr, po, dp, st, cudaMemcpyDeviceToHost)) != LFD_OK) return s;
     if (depth_out_host)
         for (int v = 0; v < V; v++)
             if (depth_out_host[v])
-                LFD_CUDA(cudaMemcpyAsync(depth_out_host[v], dp.p[v],
+                LFD_CUDA(cudaMemcpyAsync(depth_out_host[v], dptr[v],
                                          4 * (size_t)lf_host->cams[v].width * lf_host->cams[v].height,
                                          cudaMemcpyDeviceToHost, st));
     return LFD_OK;
 }
 
+lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs, const lfd_params *params,
+                              float *const *const *planes_out, float *const *const *depth_out,
+                              const lfd_batch_options *options, void *stream)
+{
+    if (!ctx) return LFD_ERR_INVALID_ARG;
+    ctx->err.clear();
+    lfd_status s;
+    if ((s = set_device(ctx)) != LFD_OK) return s;
+    lfd_batch_options o;
+    lfd_batch_options_default(&o);
+    if (options) o = *options;
+    if ((s = apply_options(ctx, o)) != LFD_OK) return s;
+    if (n < 1 || !lfs || !params) return fail(ctx, LFD_ERR_INVALID_ARG, "need n >= 1 light fields and parameters");
+    if (!planes_out) return fail(ctx, LFD_ERR_INVALID_ARG, "planes_out is NULL");
+    for (int l = 0; l < n; l++)
+        if (!planes_out[l]) return fail(ctx, LFD_ERR_INVALID_ARG, "planes_out[%d] is NULL", l);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (o.graph && !st) return fail(ctx, LFD_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    for (int l = 0; l < n; l++)
+        if (!lfs[l].num_views || lfs[l].num_views > LFD_MAX_VIEWS || !lfs[l].cams || !lfs[l].views || !lfs[l].labels ||
+            !lfs[l].grid_w || !lfs[l].grid_h)
+            return fail(ctx, LFD_ERR_INVALID_ARG, "light field %d is incomplete", l);
+    const uint64_t sig = batch_signature(n, lfs, params, planes_out, depth_out, &o);
+
+    if (o.graph && ctx->gexec && ctx->gsig == sig && ctx->bound) {     // replay
+        if (ctx->ev_bdepth) LFD_CUDA(cudaEventSynchronize(ctx->ev_bdepth));
+        LFD_CUDA(cudaGraphLaunch(ctx->gexec, st));
+        LFD_CUDA(cudaEventRecord(ctx->ev_stage, st));
+        LFD_CUDA(cudaEventRecord(ctx->ev_bdepth, st));
+        for (int k = 0; k < LFD_STAGES; k++) ctx->launches[k] += ctx->glaunches[k];
+        return LFD_OK;
+    }
+
+    drop_graph(ctx);
+    ctx->bound = false;
+    if ((s = plan_input(ctx, n, lfs, params, false)) != LFD_OK) return s;
+    int total_views = 0;
+    for (int l = 0; l < n; l++) total_views += lfs[l].num_views;
+    std::vector<float *> depth_flat(total_views, nullptr);
+    if (depth_out)
+        for (int l = 0, g = 0; l < n; l++)
+            for (int v = 0; v < lfs[l].num_views; v++, g++) depth_flat[g] = depth_out[l] ? depth_out[l][v] : nullptr;
+
+    if (o.autotune && ctx->tuned_sig != sig) {
+        // the launch shapes are timed on this input, bound outside any capture
+        const int kept_sweep = ctx->lc.sweep_persistent, kept_prop = ctx->lc.prop_persistent;
+        ctx->lc.sweep_persistent = ctx->lc.prop_persistent = 0;
+        if ((s = enqueue_input(ctx, st, true)) != LFD_OK) return s;
+        ctx->lc.sweep_persistent = kept_sweep;
+        ctx->lc.prop_persistent = kept_prop;
+        if ((s = autotune(ctx, st)) != LFD_OK) return s;
+        LFD_CUDA(cudaMemsetAsync(ctx->d_ctr, 0, 2 * sizeof(unsigned long long), st));
+        ctx->tuned_sig = sig;
+    }
+
+    if (!o.graph) {
+        if ((s = enqueue_input(ctx, st, true)) != LFD_OK) return s;
+        float **dp = nullptr;
+        if ((s = upload_depth_ptrs(ctx, depth_out ? depth_flat.data() : nullptr, st, &dp)) != LFD_OK) return s;
+        if ((s = enqueue_frame(ctx, nullptr, planes_out, dp, st, cudaMemcpyDeviceToDevice)) != LFD_OK) return s;
+        ctx->bound = true;
+        return LFD_OK;
+    }
+
+    // capture: records and the depth table are read from pinned buffers that
+    // stay unchanged while the signature does
+    if (depth_out) {
+        if (ctx->ev_bdepth) LFD_CUDA(cudaEventSynchronize(ctx->ev_bdepth));
+        if (ctx->h_bdepth_cap < total_views) {
+            if (ctx->h_bdepth) cudaFreeHost(ctx->h_bdepth);
+            ctx->h_bdepth = nullptr;
+            ctx->h_bdepth_cap = 0;
+            LFD_CUDA(cudaMallocHost(&ctx->h_bdepth, sizeof(float *) * total_views));
+            ctx->h_bdepth_cap = total_views;
+        }
+        for (int g = 0; g < total_views; g++) ctx->h_bdepth[g] = depth_flat[g];
+    }
+    long long before[LFD_STAGES];
+    for (int k = 0; k < LFD_STAGES; k++) before[k] = ctx->launches[k];
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    LFD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    s = enqueue_input(ctx, st, false);
+    if (s == LFD_OK && depth_out) {
+        const cudaError_t e = cudaMemcpyAsync(ctx->d_depth_ptrs, ctx->h_bdepth, sizeof(float *) * total_views,
+                                              cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) s = fail(ctx, LFD_ERR_CUDA, "depth table copy: %s", cudaGetErrorString(e));
+    }
+    if (s == LFD_OK)
+        s = enqueue_frame(ctx, nullptr, planes_out, depth_out ? ctx->d_depth_ptrs : nullptr, st,
+                          cudaMemcpyDeviceToDevice);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+    ctx->prof = prof;
+    if (s != LFD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return s;
+    }
+    if (ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(ctx, LFD_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ec));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        ctx->gexec = nullptr;
+        cudaGetLastError();
+        return fail(ctx, LFD_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    }
+    for (int k = 0; k < LFD_STAGES; k++) ctx->glaunches[k] = ctx->launches[k] - before[k];
+    ctx->gsig = sig;
+    LFD_CUDA(cudaGraphLaunch(ctx->gexec, st));
+    LFD_CUDA(cudaEventRecord(ctx->ev_stage, st));
+    LFD_CUDA(cudaEventRecord(ctx->ev_bdepth, st));
+    ctx->bound = true;
+    return LFD_OK;
+}
+
+lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out)
+{
+    if (!ctx || !out) return LFD_ERR_INVALID_ARG;
+    out[0] = ctx->lc.sweep_threads;
+    out[1] = ctx->lc.sweep_persistent;
+    out[2] = ctx->lc.prop_blocks;
+    out[3] = ctx->lc.prop_persistent;
+    return LFD_OK;
+}
 lfd_status lfd_synchronize(lfd_ctx *ctx, void *stream)
 {
     if (!ctx) return LFD_ERR_INVALID_ARG;

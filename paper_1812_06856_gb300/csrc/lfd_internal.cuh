@@ -34,12 +34,27 @@ struct ViewDev {
     long long px_base;
     int nnb;
     int ksize_init, ksteps_init;
-    int pad0;
+    int lf;                  // light field this view belongs to
     double Kinv[9];
     double wz[3];            // world z axis in this camera's frame (R e3), for world-frame sweeps
     const int *labels;       // caller label map (valid during lfd_set_input only)
+    const void *img;         // caller image (valid during lfd_set_input only)
+    long long pitch;         // its row pitch in bytes
     void *quad;              // sampling texture (format dependent)
     float4 *map;             // rasterised {colour, depth value}
+    // parameters of the view's light field
+    int L, jitter, lf_index, term_mask;
+    int iters, warm_off;
+    int lv;                  // index of the view within its light field (jitter key)
+    int pad2;
+    unsigned long long seed;
+    double inv_dmin, inv_dmax, delta;   // delta: inverse-depth bin width
+    float T;                 // Eq. 1 truncation in the sampler's colour units squared
+    float k_col;             // log2(e) / (2 alpha^2)     (Eq. 7)
+    float k_sig;             // log2(e) / (2 sigma^2)     (Eq. 6, Eq. 10)
+    float eta;               // Eq. 11
+    float xy_lo, xy_hi;      // X/Y split: inverse domain X iff zeta >= D xy_lo; depth domain X iff z <= D xy_hi
+    float pad3, pad4;
 };
 
 // view v -> its k-th neighbour view i.  The plane with inverse-depth vector g
@@ -64,18 +79,13 @@ struct DevCounters {
     int bad_view, bad_index, pad;
 };
 
-// constant parameters of a launch
+// parameters shared by every view of a launch (the rest is per view in ViewDev)
 struct Consts {
-    int V, L, fmt, domain;
-    int jitter, term_mask, sweep_frame, lf_index;
-    unsigned long long seed;
-    double d_min, d_max, inv_dmin, inv_dmax, delta;   // delta: inverse-depth bin width
-    float T;                 // Eq. 1 truncation (in the sampler's colour units squared)
+    int V, L, fmt, domain;   // L: label count of single-light-field calls (cost_out stride)
+    int sweep_frame;
+    int batch_iters;         // 1: a view whose light field has run its iterations passes its plane through
     float col_scale;         // sampler colour units -> [0,1]
-    float k_col;             // log2(e) / (2 alpha^2)     (Eq. 7)
-    float k_sig;             // log2(e) / (2 sigma^2)     (Eq. 6, Eq. 10)
-    float eta, xy_lo, xy_hi; // X/Y split factors: inverse domain X iff zeta >= D/(1+eps); depth domain X iff z <= D(1+eps)
-    int pad;
+    float pad1;
 };
 
 struct Workspace {
@@ -93,6 +103,8 @@ struct Workspace {
     const short *radii;      // [V][LFD_MAX_ITER_INDEX + 1][LFD_MAX_RADII]
     const int *radii_cnt;    // [V][LFD_MAX_ITER_INDEX + 1]
     DevCounters *ctr;
+    const int *order;        // [S_total] superpixels by descending cost (persistent launches)
+    int *queue;              // [4] work-queue counters of persistent launches
     int S_total;
     long long px_total;
 };
@@ -162,32 +174,30 @@ __device__ __forceinline__ void ring_dir(int d, int &dx, int &dy)
     }
 }
 
-}  // namespace lfd
-
-// pointer tables passed by value as kernel parameters
-struct ViewPtrs {
-    const void *p[LFD_MAX_VIEWS];
-    long long pitch[LFD_MAX_VIEWS];
-};
-struct OutPtrs {
-    float *p[LFD_MAX_VIEWS];
+// launch shape of the two hot kernels (chosen by the autotuner)
+struct LaunchCfg {
+    int sweep_threads;       // 128 or 256 threads (labels) per CTA
+    int sweep_persistent;    // 1: persistent CTAs over a cost-ordered queue
+    int prop_blocks;         // 7 or 8 resident 4-warp CTAs per SM (register budget)
+    int prop_persistent;     // 1: persistent warps over a cost-ordered queue
+    int num_sms;
 };
 
-// launchers (defined in the kernel translation units); every buffer is the
-// context's flat workspace array indexed by global superpixel / pixel number
-namespace lfd {
 cudaError_t launch_sp_count(const Workspace &w, int V, int max_px, int *cnt, int4 *bbox, cudaStream_t st);
 cudaError_t launch_sp_scan(const Workspace &w, int V, const int *cnt, int *off, cudaStream_t st);
-cudaError_t launch_sp_collect(const Workspace &w, const Consts &c, const ViewPtrs &img, const int4 *bbox,
-                              const int *cnt, unsigned *pix, double2 *cen, int2 *ref, float4 *col, cudaStream_t st);
+cudaError_t launch_sp_collect(const Workspace &w, const Consts &c, const int4 *bbox, const int *cnt, unsigned *pix,
+                              double2 *cen, int2 *ref, float4 *col, cudaStream_t st);
 cudaError_t launch_sp_minw(const Workspace &w, const Consts &c, float4 *col, cudaStream_t st);
-cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, const ViewPtrs &img, cudaStream_t st);
-cudaError_t launch_sweep(const Workspace &w, const Consts &c, float4 *planes, int *label, float *cost, cudaStream_t st);
+cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStream_t st);
+cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, cudaStream_t st);
+cudaError_t launch_sweep(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
+                         float *cost, cudaStream_t st);
 cudaError_t launch_plane_prep(const Workspace &w, const Consts &c, const float4 *planes, double4_32a *g, float4 *rc,
                               cudaStream_t st);
-cudaError_t launch_rasterize(const Workspace &w, const Consts &c, const OutPtrs *depth, cudaStream_t st);
-cudaError_t launch_propagate(const Workspace &w, const Consts &c, int iter_eff, const float4 *planes_in,
-                             float4 *planes_out, int *choice, float *energy, cudaStream_t st);
+cudaError_t launch_rasterize(const Workspace &w, const Consts &c, float *const *depth, cudaStream_t st);
+cudaError_t launch_propagate(const Workspace &w, const Consts &c, const LaunchCfg &lc, int iter,
+                             const float4 *planes_in, float4 *planes_out, int *choice, float *energy,
+                             cudaStream_t st);
 cudaError_t launch_score(const Workspace &w, const Consts &c, const float4 *planes_state, int nq, const lfd_query *q,
                          float *out, cudaStream_t st);
 }  // namespace lfd

@@ -53,6 +53,12 @@ class Query(C.Structure):
                 ("ny", C.c_float), ("nz", C.c_float)]
 
 
+class BatchOptions(C.Structure):
+    _fields_ = [("autotune", C.c_int32), ("graph", C.c_int32), ("sweep_threads", C.c_int32),
+                ("sweep_persistent", C.c_int32), ("prop_blocks", C.c_int32), ("prop_persistent", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
+
+
 class LfdError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"lfdepth status {status}: {msg}")
@@ -103,15 +109,19 @@ def load(build_if_missing: bool = True):
     lib.lfd_superpixel_stats_noalloc.restype = i32
     lib.lfd_kernel_offsets.restype = i32
     lib.lfd_kernel_offsets.argtypes = [i32, i32, i32, P(i32), i32]
+    lib.lfd_batch_options_default.argtypes = [P(BatchOptions)]
+    lib.lfd_batch_options_default.restype = None
+    lib.lfd_estimate_batch.argtypes = [vp, i32, P(LightFieldC), P(Params), P(vp), P(vp), P(BatchOptions), vp]
+    lib.lfd_launch_config.argtypes = [vp, P(i32)]
     for name in ("lfd_create", "lfd_destroy", "lfd_set_input", "lfd_num_superpixels", "lfd_plane_sweep",
                  "lfd_rasterize", "lfd_iterate", "lfd_estimate", "lfd_estimate_host", "lfd_synchronize",
                  "lfd_counters", "lfd_score", "lfd_get_superpixels", "lfd_neighbor_views", "lfd_profile_enable",
-                 "lfd_profile_read"):
+                 "lfd_profile_read", "lfd_estimate_batch", "lfd_launch_config"):
         getattr(lib, name).restype = i32
-    sizes = (i32 * 4)()
+    sizes = (i32 * 8)()
     lib.lfd_struct_sizes(sizes)
-    want = [C.sizeof(Camera), C.sizeof(LightFieldC), C.sizeof(Params), C.sizeof(Query)]
-    if list(sizes) != want:
+    want = [C.sizeof(Camera), C.sizeof(LightFieldC), C.sizeof(Params), C.sizeof(Query), C.sizeof(BatchOptions)]
+    if list(sizes)[:5] != want:
         raise RuntimeError(f"lfdepth ABI mismatch: library struct sizes {list(sizes)} != binding {want}")
     _lib = lib
     return lib
@@ -242,6 +252,7 @@ class Context:
         self.sp_base = np.concatenate([[0], np.cumsum(self.S)[:-1]]).astype(np.int64)
         self.S_total = int(self.S.sum())
         self.V = V
+        self.view_hw = None
 
     def _view_ptrs(self, flat: torch.Tensor, per_sp: int):
         assert flat.is_cuda and flat.is_contiguous()
@@ -338,6 +349,74 @@ class Context:
         self._check(self.lib.lfd_estimate_host(self.h, C.byref(lf), C.byref(p), pp, dptr, _stream(stream)),
                     "lfd_estimate_host")
 
+    def estimate_batch(self, items, options: dict | None = None, want_depth: bool = True, out=None,
+                       stream=None):
+        """Several light fields in one pass (lfd_estimate_batch).
+
+        items: list of dicts with keys views, labels, K, R, t, GW, GH, params
+        (as for `estimate`).  options: lfd_batch_options fields.  out: the
+        (planes, depths) returned by an earlier call with the same items, to
+        write into the same buffers (a graph replay needs identical pointers).
+        Returns (planes, depths): planes (S_total, 4) over all light fields'
+        superpixels in order; depths a list of (V_l, H_l, W_l) tensors or None."""
+        n = len(items)
+        lfs = (LightFieldC * n)()
+        ps = (Params * n)()
+        keep = []
+        S_all, V_all = [], 0
+        for l, it in enumerate(items):
+            lf, k = self._lightfield(it["views"], it["labels"], it["K"], it["R"], it["t"], it["GW"], it["GH"])
+            lfs[l] = lf
+            ps[l] = params_struct(it["params"])
+            keep.append(k)
+            V = len(it["K"])
+            gw = [int(it["GW"])] * V if np.isscalar(it["GW"]) else [int(x) for x in it["GW"]]
+            gh = [int(it["GH"])] * V if np.isscalar(it["GH"]) else [int(x) for x in it["GH"]]
+            S_all += [a * b for a, b in zip(gw, gh)]
+            V_all += V
+        self.S = np.array(S_all, dtype=np.int64)
+        self.sp_base = np.concatenate([[0], np.cumsum(self.S)[:-1]]).astype(np.int64)
+        self.S_total = int(self.S.sum())
+        self.V = V_all
+        self.H, self.W = int(items[0]["views"].shape[1]), int(items[0]["views"].shape[2])
+        self.view_hw = [(int(it["views"].shape[1]), int(it["views"].shape[2])) for it in items
+                        for _ in range(len(it["K"]))]
+        self.params = dict(items[0]["params"])
+        dev = items[0]["views"].device
+        if out is not None:
+            planes, depths = out
+        else:
+            planes = torch.zeros((self.S_total, 4), dtype=torch.float32, device=dev)
+            depths = [torch.zeros((len(it["K"]), int(it["views"].shape[1]), int(it["views"].shape[2])),
+                                  dtype=torch.float32, device=dev) for it in items] if want_depth else None
+        pp_all = self._view_ptrs(planes, 4)
+        pp = (C.c_void_p * n)()
+        dd = (C.c_void_p * n)()
+        g = 0
+        for l, it in enumerate(items):
+            V = len(it["K"])
+            arr = _ptr_array([pp_all[g + v] for v in range(V)])
+            pp[l] = C.cast(arr, C.c_void_p)
+            keep.append(arr)
+            if depths is not None:
+                darr = _ptr_array([depths[l][v].data_ptr() for v in range(V)])
+                dd[l] = C.cast(darr, C.c_void_p)
+                keep.append(darr)
+            g += V
+        o = BatchOptions()
+        self.lib.lfd_batch_options_default(C.byref(o))
+        for key, val in (options or {}).items():
+            setattr(o, key, int(val))
+        self._keep = [keep, lfs, ps, pp_all, pp, dd, o, planes, depths]
+        self._check(self.lib.lfd_estimate_batch(self.h, n, lfs, ps, pp, dd if depths is not None else None,
+                                                C.byref(o), _stream(stream)), "lfd_estimate_batch")
+        return planes, depths
+
+    def launch_config(self) -> dict:
+        out = (C.c_int32 * 4)()
+        self._check(self.lib.lfd_launch_config(self.h, out), "lfd_launch_config")
+        return dict(sweep_threads=out[0], sweep_persistent=out[1], prop_blocks=out[2], prop_persistent=out[3])
+
     def synchronize(self, stream=None):
         self._check(self.lib.lfd_synchronize(self.h, _stream(stream)), "lfd_synchronize")
 
@@ -370,7 +449,8 @@ class Context:
     def get_superpixels(self, view: int) -> dict:
         S = int(self.S[view])
         off = np.zeros(S + 1, np.int32)
-        pix = np.zeros(self.H * self.W, np.int32)
+        h, w = self.view_hw[view] if getattr(self, "view_hw", None) else (self.H, self.W)
+        pix = np.zeros(h * w, np.int32)
         stats = np.zeros((S, 8), np.float32)
         nb = np.zeros(MAX_NEIGHBOR_VIEWS, np.int32)
         self._check(self.lib.lfd_get_superpixels(self.h, view, off.ctypes.data, pix.ctypes.data, stats.ctypes.data,
