@@ -70,7 +70,7 @@ enum {
     LFD_ERR_BUDGET = 4,        /* the workspace would exceed the context's HBM budget */
     LFD_ERR_TIMEOUT = 5,       /* a bounded wait ran out */
     LFD_ERR_DEVICE_CHECK = 6,  /* a device-side input check failed (see lfd_last_error) */
-    LFD_ERR_BUSY = 7,
+    LFD_ERR_BUSY = 7,           /* a queue bound was reached (lfd_server_submit) */
     LFD_ERR_STATE = 8          /* call order: e.g. lfd_iterate before lfd_set_input */
 };
 
@@ -274,9 +274,78 @@ lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs
                               float *const *const *planes_out, float *const *const *depth_out,
                               const lfd_batch_options *options, void *stream);
 
+/* Device workspace (bytes) that binding these n light fields allocates: the
+ * figure lfd_create's hbm_budget_bytes is checked against.  Reads only the
+ * cameras, grid sizes and pixel format. */
+lfd_status lfd_workspace_required(int32_t n, const lfd_lightfield *lfs, uint64_t *bytes);
+
 /* The launch shape in use: out[0..3] = sweep_threads, sweep_persistent,
  * prop_blocks, prop_persistent. */
 lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out);
+
+/* ---- serving ---------------------------------------------------------- */
+
+/* A frame server: several rigs (camera arrays, each a stream of light-field
+ * frames) share one GPU.  A server owns `max_slots` slots, each a context with
+ * its own CUDA stream; frames of different rigs run concurrently on different
+ * slots, frames of one rig run in submission order on the rig's slot.
+ *
+ * Warm start (not in the paper, where every frame is independent): the first
+ * frame of a rig (or the first after its layout changes) runs the plane sweep
+ * and params->iterations iterations; every later frame starts from the rig's
+ * previous planes and runs warm_iterations iterations with
+ * warm_iter_offset added to the iteration index of Eq. 4 (defaults 3 and 3:
+ * the small kernels of I = 4..6).  warm_iterations = 0 makes every frame cold.
+ *
+ * Admission: a rig is bound to the slot with the fewest rigs when first seen;
+ * a slot's workspace is the largest lfd_workspace_required() of its rigs; the
+ * sum over slots plus the rigs' plane states must stay within
+ * hbm_budget_bytes (0 = no bound), else the submit fails with LFD_ERR_BUDGET.
+ * At most max_pending_per_rig frames of a rig may be in flight; a submit
+ * beyond that returns LFD_ERR_BUSY (the caller drops or retries the frame).
+ * The server is not thread safe. */
+typedef struct lfd_server lfd_server;
+
+typedef struct {
+    uint64_t req_id;
+    int32_t rig_id;
+    int32_t warm;              /* 1: started from the rig's previous planes */
+    int64_t frame;             /* 0-based frame count of the rig */
+    int64_t submit_ns;         /* lfd_server_now_ns() at submission */
+    int64_t done_ns;           /* lfd_server_now_ns() when the stream reached the end of the frame */
+    lfd_status status;
+    int32_t slot;
+} lfd_result;
+
+lfd_status lfd_server_create(lfd_server **out, int32_t device, uint64_t hbm_budget_bytes, int32_t max_slots);
+lfd_status lfd_server_destroy(lfd_server *srv);            /* waits for all frames */
+const char *lfd_server_last_error(const lfd_server *srv);
+/* Warm-start schedule and queue bound (defaults 3, 3, 2). */
+lfd_status lfd_server_configure(lfd_server *srv, int32_t warm_iterations, int32_t warm_iter_offset,
+                                int32_t max_pending_per_rig);
+/* Monotonic clock of the result timestamps, in ns. */
+int64_t lfd_server_now_ns(void);
+
+/* Queue one frame of rig `rig_id` (>= 0).  lf and params as for lfd_estimate
+ * (device images and labels, which must stay unchanged until the frame is
+ * done); planes_out / depth_out are host arrays [V] of device buffers or NULL.
+ * The rig's plane state is kept by the server.  Returns at once with
+ * *req_id. */
+lfd_status lfd_server_submit(lfd_server *srv, int32_t rig_id, const lfd_lightfield *lf, const lfd_params *params,
+                             float *const *planes_out, float *const *depth_out, uint64_t *req_id);
+/* Wait up to timeout_us (0 = just test, < 0 = no limit) for request req_id.
+ * LFD_OK fills *out and forgets the request; LFD_ERR_TIMEOUT if it is still
+ * running; LFD_ERR_INVALID_ARG for an unknown id. */
+lfd_status lfd_server_poll(lfd_server *srv, uint64_t req_id, int32_t timeout_us, lfd_result *out);
+/* The plane state of rig `rig_id` (all views' superpixels in order, float4
+ * each) to host memory after its queued frames (synchronous); *n_sp gets
+ * the superpixel count; planes_host may be NULL to query it. */
+lfd_status lfd_server_export_state(lfd_server *srv, int32_t rig_id, float *planes_host, int64_t cap_sp,
+                                   int64_t *n_sp);
+/* Replace rig `rig_id`'s plane state (e.g. exported from another server);
+ * its next frame starts warm from it.  The rig must have submitted a frame
+ * (its layout is known) and n_sp must match. */
+lfd_status lfd_server_import_state(lfd_server *srv, int32_t rig_id, const float *planes_host, int64_t n_sp);
 
 /* Wait for the stream and report device-side check failures
  * (LFD_ERR_DEVICE_CHECK) raised by this context's kernels; clears them. */

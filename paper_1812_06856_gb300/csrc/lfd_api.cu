@@ -111,6 +111,51 @@ struct Arena {
     }
 };
 
+// Pinned host staging for uploads that must not block the caller: a ring of
+// buffers, each reused only once the upload that last read it has finished,
+// so a caller can queue several frames on a busy stream without waiting.
+struct PinnedRing {
+    static constexpr int N = 4;
+    void *p[N] = {};
+    size_t cap[N] = {};
+    cudaEvent_t ev[N] = {};
+    int cur = 0;
+    cudaError_t init()
+    {
+        for (cudaEvent_t &e : ev) {
+            const cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    }
+    // advance to the next buffer, grown to `bytes`, after its last upload
+    cudaError_t next(size_t bytes)
+    {
+        cur = (cur + 1) % N;
+        cudaError_t r = cudaEventSynchronize(ev[cur]);
+        if (r != cudaSuccess) return r;
+        if (cap[cur] >= bytes) return cudaSuccess;
+        if (p[cur]) cudaFreeHost(p[cur]);
+        p[cur] = nullptr;
+        cap[cur] = 0;
+        r = cudaMallocHost(&p[cur], bytes);
+        if (r == cudaSuccess) cap[cur] = bytes;
+        return r;
+    }
+    void *buf() const { return p[cur]; }
+    cudaEvent_t event() const { return ev[cur]; }
+    void release()
+    {
+        for (int i = 0; i < N; i++) {
+            if (ev[i]) cudaEventSynchronize(ev[i]);
+            if (p[i]) cudaFreeHost(p[i]);
+            if (ev[i]) cudaEventDestroy(ev[i]);
+            p[i] = nullptr;
+            ev[i] = nullptr;
+        }
+    }
+};
+
 struct Layout {
     int V = 0;
     std::vector<int> W, H, GW, GH, S, sp_base;
@@ -177,12 +222,8 @@ struct lfd_ctx {
     std::vector<cudaEvent_t> prof_free;
     long long launches[LFD_STAGES] = {0, 0, 0, 0};
     // pinned upload staging (records) and depth-pointer table
-    void *h_stage = nullptr;
-    size_t h_stage_cap = 0;
-    cudaEvent_t ev_stage = nullptr;
-    float **h_depth = nullptr;
-    int h_depth_cap = 0;
-    cudaEvent_t ev_depth = nullptr;
+    PinnedRing stage;                // view/pair/radii records
+    PinnedRing dtab;                 // depth-output pointer tables
     // CUDA graph of a batched frame and the pinned depth table it reads
     cudaGraphExec_t gexec = nullptr;
     uint64_t gsig = 0;
@@ -312,13 +353,7 @@ void view_params(ViewDev &d, const lfd_params &p, int fmt, int lf)
 
 lfd_status ensure_pinned(lfd_ctx *ctx, size_t bytes)
 {
-    if (ctx->ev_stage) LFD_CUDA(cudaEventSynchronize(ctx->ev_stage));   // previous upload has left the buffer
-    if (ctx->h_stage_cap >= bytes) return LFD_OK;
-    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-    ctx->h_stage = nullptr;
-    ctx->h_stage_cap = 0;
-    LFD_CUDA(cudaMallocHost(&ctx->h_stage, bytes));
-    ctx->h_stage_cap = bytes;
+    LFD_CUDA(ctx->stage.next(bytes));
     return LFD_OK;
 }
 
@@ -373,9 +408,10 @@ cudaError_t traced(lfd_ctx *ctx, int stage, cudaStream_t st, F launch)
 // -- layout + workspace allocation -------------------------------------------
 constexpr int ORDER_BUCKETS_HOST = 1024;
 
-lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
+// Sizes of the bound views in call order (global numbering).
+lfd_status make_layout(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, Layout &L)
 {
-    Layout L;
+    L = Layout();
     for (int l = 0; l < n; l++)
         for (int v = 0; v < lfs[l].num_views; v++) {
             const lfd_camera &c = lfs[l].cams[v];
@@ -394,9 +430,15 @@ lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
             L.V++;
         }
     if (L.px_total >= (1LL << 31)) return fail(ctx, LFD_ERR_INVALID_ARG, "more than 2^31 pixels in one call");
+    return LFD_OK;
+}
+
+// Device workspace of a layout, in bytes (the arena carved by plan_workspace).
+size_t workspace_need(const Layout &L, int fmt)
+{
     const int V = L.V;
     const size_t S = L.S_total, P = (size_t)L.px_total;
-    const int qb = quad_bytes(lfs[0].fmt);
+    const int qb = quad_bytes(fmt);
     size_t need = 0;
     auto add = [&](size_t b) { need = align_up(need, 256) + b; };
     add(sizeof(ViewDev) * V);
@@ -410,7 +452,18 @@ lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
     add(16 * S); add(16 * S); add(4 * S); add(8 * S); add(8 * S);
     for (int v = 0; v < V; v++) add((size_t)qb * L.W[v] * L.H[v]);
     for (int v = 0; v < V; v++) add((size_t)16 * L.W[v] * L.H[v]);
-    need += 256;
+    return need + 256;
+}
+
+lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
+{
+    Layout L;
+    lfd_status s;
+    if ((s = make_layout(ctx, n, lfs, L)) != LFD_OK) return s;
+    const int V = L.V;
+    const size_t S = L.S_total, P = (size_t)L.px_total;
+    const int qb = quad_bytes(lfs[0].fmt);
+    const size_t need = workspace_need(L, lfs[0].fmt);
     if (ctx->budget && need > ctx->budget)
         return fail(ctx, LFD_ERR_BUDGET, "workspace needs %zu bytes, budget is %llu", need,
                     (unsigned long long)ctx->budget);
@@ -534,7 +587,7 @@ lfd_status plan_input(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, const lfd_
         (char *)ctx->d_radii_cnt - (char *)ctx->d_views != (ptrdiff_t)o_rcnt)
         return fail(ctx, LFD_ERR_STATE, "internal: workspace record layout mismatch");
     if ((s = ensure_pinned(ctx, total)) != LFD_OK) return s;
-    char *h = (char *)ctx->h_stage;
+    char *h = (char *)ctx->stage.buf();
     memset(h, 0, total);
     ViewDev *hv = (ViewDev *)h;
     PairDev *hp = (PairDev *)(h + o_pairs);
@@ -625,8 +678,8 @@ lfd_status enqueue_input(lfd_ctx *ctx, cudaStream_t st, bool record_event)
     const Layout &L = ctx->L;
     const int V = L.V;
     const size_t total = (char *)(ctx->d_radii_cnt + (size_t)V * (LFD_MAX_ITER_INDEX + 1)) - (char *)ctx->d_views;
-    LFD_CUDA(cudaMemcpyAsync(ctx->d_views, ctx->h_stage, total, cudaMemcpyHostToDevice, st));
-    if (record_event) LFD_CUDA(cudaEventRecord(ctx->ev_stage, st));
+    LFD_CUDA(cudaMemcpyAsync(ctx->d_views, ctx->stage.buf(), total, cudaMemcpyHostToDevice, st));
+    if (record_event) LFD_CUDA(cudaEventRecord(ctx->stage.event(), st));
     LFD_CUDA(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
     for (int v = 0; v < V; v++) {
         LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
@@ -704,17 +757,11 @@ lfd_status upload_depth_ptrs(lfd_ctx *ctx, float *const *per_view, cudaStream_t 
     *dev_out = nullptr;
     if (!per_view) return LFD_OK;
     const int V = ctx->L.V;
-    if (ctx->ev_depth) LFD_CUDA(cudaEventSynchronize(ctx->ev_depth));
-    if (ctx->h_depth_cap < V) {
-        if (ctx->h_depth) cudaFreeHost(ctx->h_depth);
-        ctx->h_depth = nullptr;
-        ctx->h_depth_cap = 0;
-        LFD_CUDA(cudaMallocHost(&ctx->h_depth, sizeof(float *) * V));
-        ctx->h_depth_cap = V;
-    }
-    for (int v = 0; v < V; v++) ctx->h_depth[v] = per_view[v];
-    LFD_CUDA(cudaMemcpyAsync(ctx->d_depth_ptrs, ctx->h_depth, sizeof(float *) * V, cudaMemcpyHostToDevice, st));
-    LFD_CUDA(cudaEventRecord(ctx->ev_depth, st));
+    LFD_CUDA(ctx->dtab.next(sizeof(float *) * V));
+    float **h = (float **)ctx->dtab.buf();
+    for (int v = 0; v < V; v++) h[v] = per_view[v];
+    LFD_CUDA(cudaMemcpyAsync(ctx->d_depth_ptrs, h, sizeof(float *) * V, cudaMemcpyHostToDevice, st));
+    LFD_CUDA(cudaEventRecord(ctx->dtab.event(), st));
     *dev_out = ctx->d_depth_ptrs;
     return LFD_OK;
 }
@@ -902,7 +949,7 @@ namespace {
 void drop_graph(lfd_ctx *ctx)
 {
     if (!ctx->gexec) return;
-    if (ctx->ev_stage) cudaEventSynchronize(ctx->ev_stage);   // the last replay has finished
+    cudaEventSynchronize(ctx->stage.event());   // the last replay has finished
     cudaGraphExecDestroy(ctx->gexec);
     ctx->gexec = nullptr;
     ctx->gsig = 0;
@@ -1006,12 +1053,12 @@ lfd_status lfd_create(lfd_ctx **out, int32_t device, uint64_t hbm_budget_bytes)
     ctx->budget = hbm_budget_bytes;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_depth, cudaEventDisableTiming) != cudaSuccess ||
+        ctx->stage.init() != cudaSuccess || ctx->dtab.init() != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_bdepth, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
-        if (ctx->ev_stage) cudaEventDestroy(ctx->ev_stage);
-        if (ctx->ev_depth) cudaEventDestroy(ctx->ev_depth);
+        ctx->stage.release();
+        ctx->dtab.release();
+        if (ctx->ev_bdepth) cudaEventDestroy(ctx->ev_bdepth);
         delete ctx;
         return LFD_ERR_CUDA;
     }
@@ -1032,11 +1079,9 @@ lfd_status lfd_destroy(lfd_ctx *ctx)
     if (ctx->d_stage_depth) cudaFree(ctx->d_stage_depth);
     if (ctx->d_q) cudaFree(ctx->d_q);
     if (ctx->d_qout) cudaFree(ctx->d_qout);
-    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-    if (ctx->h_depth) cudaFreeHost(ctx->h_depth);
+    ctx->stage.release();
+    ctx->dtab.release();
     if (ctx->h_bdepth) cudaFreeHost(ctx->h_bdepth);
-    if (ctx->ev_stage) cudaEventDestroy(ctx->ev_stage);
-    if (ctx->ev_depth) cudaEventDestroy(ctx->ev_depth);
     if (ctx->ev_bdepth) cudaEventDestroy(ctx->ev_bdepth);
     for (auto &u : ctx->prof_used) {
         cudaEventDestroy(u.second.first);
@@ -1235,7 +1280,7 @@ lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs
     if (o.graph && ctx->gexec && ctx->gsig == sig && ctx->bound) {     // replay
         if (ctx->ev_bdepth) LFD_CUDA(cudaEventSynchronize(ctx->ev_bdepth));
         LFD_CUDA(cudaGraphLaunch(ctx->gexec, st));
-        LFD_CUDA(cudaEventRecord(ctx->ev_stage, st));
+        LFD_CUDA(cudaEventRecord(ctx->stage.event(), st));
         LFD_CUDA(cudaEventRecord(ctx->ev_bdepth, st));
         for (int k = 0; k < LFD_STAGES; k++) ctx->launches[k] += ctx->glaunches[k];
         return LFD_OK;
@@ -1322,9 +1367,22 @@ lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs
     for (int k = 0; k < LFD_STAGES; k++) ctx->glaunches[k] = ctx->launches[k] - before[k];
     ctx->gsig = sig;
     LFD_CUDA(cudaGraphLaunch(ctx->gexec, st));
-    LFD_CUDA(cudaEventRecord(ctx->ev_stage, st));
+    LFD_CUDA(cudaEventRecord(ctx->stage.event(), st));
     LFD_CUDA(cudaEventRecord(ctx->ev_bdepth, st));
     ctx->bound = true;
+    return LFD_OK;
+}
+
+lfd_status lfd_workspace_required(int32_t n, const lfd_lightfield *lfs, uint64_t *bytes)
+{
+    if (n < 1 || !lfs || !bytes) return LFD_ERR_INVALID_ARG;
+    for (int l = 0; l < n; l++)
+        if (lfs[l].num_views < 1 || lfs[l].num_views > LFD_MAX_VIEWS || !lfs[l].cams || !lfs[l].grid_w ||
+            !lfs[l].grid_h || quad_bytes(lfs[l].fmt) == 0 || lfs[l].fmt != lfs[0].fmt)
+            return LFD_ERR_INVALID_ARG;
+    Layout L;
+    if (make_layout(nullptr, n, lfs, L) != LFD_OK) return LFD_ERR_INVALID_ARG;
+    *bytes = (uint64_t)workspace_need(L, lfs[0].fmt);
     return LFD_OK;
 }
 

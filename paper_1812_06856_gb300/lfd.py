@@ -22,6 +22,10 @@ TERMS_HEAD = 4
 TERMS_PER_VIEW = 6
 TERMS_STRIDE = TERMS_HEAD + MAX_NEIGHBOR_VIEWS * TERMS_PER_VIEW
 
+LFD_ERR_BUDGET = 4
+LFD_ERR_TIMEOUT = 5
+LFD_ERR_BUSY = 7
+
 FMT = {"rgba8": 0, "rgba_f16": 1, "rgba_bf16": 2, "rgba_f32": 3}
 _DTYPE_FMT = {torch.uint8: 0, torch.float16: 1, torch.bfloat16: 2, torch.float32: 3}
 _TEXEL = {0: 4, 1: 8, 2: 8, 3: 16}
@@ -57,6 +61,11 @@ class BatchOptions(C.Structure):
     _fields_ = [("autotune", C.c_int32), ("graph", C.c_int32), ("sweep_threads", C.c_int32),
                 ("sweep_persistent", C.c_int32), ("prop_blocks", C.c_int32), ("prop_persistent", C.c_int32),
                 ("reserved", C.c_int32 * 2)]
+
+
+class Result(C.Structure):
+    _fields_ = [("req_id", C.c_uint64), ("rig_id", C.c_int32), ("warm", C.c_int32), ("frame", C.c_int64),
+                ("submit_ns", C.c_int64), ("done_ns", C.c_int64), ("status", C.c_int32), ("slot", C.c_int32)]
 
 
 class LfdError(RuntimeError):
@@ -113,10 +122,24 @@ def load(build_if_missing: bool = True):
     lib.lfd_batch_options_default.restype = None
     lib.lfd_estimate_batch.argtypes = [vp, i32, P(LightFieldC), P(Params), P(vp), P(vp), P(BatchOptions), vp]
     lib.lfd_launch_config.argtypes = [vp, P(i32)]
+    lib.lfd_workspace_required.argtypes = [i32, P(LightFieldC), P(C.c_uint64)]
+    lib.lfd_server_create.argtypes = [P(vp), i32, C.c_uint64, i32]
+    lib.lfd_server_destroy.argtypes = [vp]
+    lib.lfd_server_last_error.argtypes = [vp]
+    lib.lfd_server_last_error.restype = C.c_char_p
+    lib.lfd_server_configure.argtypes = [vp, i32, i32, i32]
+    lib.lfd_server_now_ns.argtypes = []
+    lib.lfd_server_now_ns.restype = C.c_int64
+    lib.lfd_server_submit.argtypes = [vp, i32, P(LightFieldC), P(Params), P(vp), P(vp), P(C.c_uint64)]
+    lib.lfd_server_poll.argtypes = [vp, C.c_uint64, i32, P(Result)]
+    lib.lfd_server_export_state.argtypes = [vp, i32, vp, C.c_int64, P(C.c_int64)]
+    lib.lfd_server_import_state.argtypes = [vp, i32, vp, C.c_int64]
     for name in ("lfd_create", "lfd_destroy", "lfd_set_input", "lfd_num_superpixels", "lfd_plane_sweep",
                  "lfd_rasterize", "lfd_iterate", "lfd_estimate", "lfd_estimate_host", "lfd_synchronize",
                  "lfd_counters", "lfd_score", "lfd_get_superpixels", "lfd_neighbor_views", "lfd_profile_enable",
-                 "lfd_profile_read", "lfd_estimate_batch", "lfd_launch_config"):
+                 "lfd_profile_read", "lfd_estimate_batch", "lfd_launch_config", "lfd_workspace_required",
+                 "lfd_server_create", "lfd_server_destroy", "lfd_server_configure", "lfd_server_submit",
+                 "lfd_server_poll", "lfd_server_export_state", "lfd_server_import_state"):
         getattr(lib, name).restype = i32
     sizes = (i32 * 8)()
     lib.lfd_struct_sizes(sizes)
@@ -199,6 +222,24 @@ def _stream(stream) -> C.c_void_p:
     return C.c_void_p(stream.cuda_stream)
 
 
+def marshal_lightfield(views, labels, K, R, t, GW, GH):
+    """lfd_lightfield of device tensors views (V,H,W,4) and labels (V,H,W) int32;
+    returns it with the ctypes arrays and tensors it points into (keep alive)."""
+    V = len(K)
+    assert views.dim() == 4 and views.shape[0] == V and views.shape[-1] == 4
+    fmt = _DTYPE_FMT[views.dtype]
+    H, W = int(views.shape[1]), int(views.shape[2])
+    cams = make_cameras(K, R, t, W, H)
+    vptr = _ptr_array([views[v].data_ptr() for v in range(V)])
+    lptr = _ptr_array([labels[v].data_ptr() for v in range(V)])
+    pitch = (C.c_int64 * V)(*([W * _TEXEL[fmt]] * V))
+    gw = (C.c_int32 * V)(*([int(GW)] * V if np.isscalar(GW) else [int(x) for x in GW]))
+    gh = (C.c_int32 * V)(*([int(GH)] * V if np.isscalar(GH) else [int(x) for x in GH]))
+    lf = LightFieldC(V, fmt, cams, vptr, pitch, lptr, gw, gh)
+    keep = (cams, vptr, lptr, pitch, gw, gh, views, labels)
+    return lf, keep
+
+
 class Context:
     """One light-field workspace on one GPU (lfd_ctx)."""
 
@@ -231,19 +272,7 @@ class Context:
 
     # -- marshalling ---------------------------------------------------------
     def _lightfield(self, views, labels, K, R, t, GW, GH):
-        V = len(K)
-        assert views.dim() == 4 and views.shape[0] == V and views.shape[-1] == 4
-        fmt = _DTYPE_FMT[views.dtype]
-        H, W = int(views.shape[1]), int(views.shape[2])
-        cams = make_cameras(K, R, t, W, H)
-        vptr = _ptr_array([views[v].data_ptr() for v in range(V)])
-        lptr = _ptr_array([labels[v].data_ptr() for v in range(V)])
-        pitch = (C.c_int64 * V)(*([W * _TEXEL[fmt]] * V))
-        gw = (C.c_int32 * V)(*([int(GW)] * V if np.isscalar(GW) else [int(x) for x in GW]))
-        gh = (C.c_int32 * V)(*([int(GH)] * V if np.isscalar(GH) else [int(x) for x in GH]))
-        lf = LightFieldC(V, fmt, cams, vptr, pitch, lptr, gw, gh)
-        keep = (cams, vptr, lptr, pitch, gw, gh, views, labels)
-        return lf, keep
+        return marshal_lightfield(views, labels, K, R, t, GW, GH)
 
     def _layout(self, V, GW, GH):
         gw = [int(GW)] * V if np.isscalar(GW) else [int(x) for x in GW]
@@ -464,3 +493,89 @@ def terms_dict(rec: np.ndarray, nviews: int) -> dict:
     per = rec[TERMS_HEAD:TERMS_HEAD + nviews * TERMS_PER_VIEW].reshape(nviews, TERMS_PER_VIEW)
     d.update(S=per[:, 0], Vt=per[:, 1], O=per[:, 2], nvalid=per[:, 3], nx=per[:, 4], ny=per[:, 5])
     return d
+
+
+class Server:
+    """Frame server (lfd_server): rigs share one GPU through `max_slots`
+    context+stream slots; later frames of a rig start warm from its previous
+    planes."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, max_slots: int = 4):
+        self.lib = load()
+        self.h = C.c_void_p()
+        st = self.lib.lfd_server_create(C.byref(self.h), device, hbm_budget, max_slots)
+        if st != 0:
+            raise LfdError(st, f"lfd_server_create: {self.lib.lfd_status_string(st).decode()}")
+        self.device = device
+        self._keep = {}
+
+    def close(self):
+        if self.h:
+            self.lib.lfd_server_destroy(self.h)
+            self.h = C.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            raise LfdError(st, f"{what}: {self.lib.lfd_status_string(st).decode()}: "
+                               f"{self.lib.lfd_server_last_error(self.h).decode()}")
+
+    @staticmethod
+    def now_ns() -> int:
+        return int(load().lfd_server_now_ns())
+
+    def configure(self, warm_iterations: int = 3, warm_iter_offset: int = 3, max_pending: int = 2):
+        self._check(self.lib.lfd_server_configure(self.h, warm_iterations, warm_iter_offset, max_pending),
+                    "lfd_server_configure")
+
+    def submit(self, rig_id: int, views, labels, K, R, t, GW, GH, params: dict, planes_out=None, depth_out=None):
+        """Queue a frame; returns the request id, or None when the rig already
+        has its maximum of frames in flight (LFD_ERR_BUSY).  planes_out is a
+        (S_total, 4) float32 cuda tensor, depth_out (V, H, W) float32, or None."""
+        lf, keep = marshal_lightfield(views, labels, K, R, t, GW, GH)
+        p = params_struct(params)
+        V = len(K)
+        pp = dd = None
+        if planes_out is not None:
+            S = [int(a) * int(b) for a, b in zip(np.broadcast_to(GW, V), np.broadcast_to(GH, V))]
+            base = np.concatenate([[0], np.cumsum(S)[:-1]])
+            pp = _ptr_array([planes_out.data_ptr() + int(b) * 16 for b in base])
+        if depth_out is not None:
+            dd = _ptr_array([depth_out[v].data_ptr() for v in range(V)])
+        rid = C.c_uint64()
+        st = self.lib.lfd_server_submit(self.h, rig_id, C.byref(lf), C.byref(p), pp, dd, C.byref(rid))
+        if st == LFD_ERR_BUSY:
+            return None
+        self._check(st, "lfd_server_submit")
+        self._keep[rid.value] = (lf, keep, p, pp, dd, planes_out, depth_out)
+        return rid.value
+
+    def poll(self, req_id: int, timeout_us: int = -1):
+        """Result dict of a finished request, or None if still running after timeout_us."""
+        r = Result()
+        st = self.lib.lfd_server_poll(self.h, req_id, timeout_us, C.byref(r))
+        if st == LFD_ERR_TIMEOUT:
+            return None
+        self._check(st, "lfd_server_poll")
+        self._keep.pop(req_id, None)
+        return dict(req_id=r.req_id, rig_id=r.rig_id, warm=r.warm, frame=r.frame, submit_ns=r.submit_ns,
+                    done_ns=r.done_ns, status=r.status, slot=r.slot)
+
+    def export_state(self, rig_id: int) -> torch.Tensor:
+        n = C.c_int64()
+        self._check(self.lib.lfd_server_export_state(self.h, rig_id, None, 0, C.byref(n)), "lfd_server_export_state")
+        out = torch.zeros((n.value, 4), dtype=torch.float32)
+        self._check(self.lib.lfd_server_export_state(self.h, rig_id, out.data_ptr(), n.value, C.byref(n)),
+                    "lfd_server_export_state")
+        return out
+
+    def import_state(self, rig_id: int, planes: torch.Tensor):
+        planes = planes.detach().to(torch.float32).cpu().contiguous()
+        self._check(self.lib.lfd_server_import_state(self.h, rig_id, planes.data_ptr(), planes.shape[0]),
+                    "lfd_server_import_state")

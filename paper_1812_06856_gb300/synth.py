@@ -557,3 +557,92 @@ def oracle_inputs(lf: LightField, rgb=None):
 def rgba8_as_float(rgba8: torch.Tensor) -> torch.Tensor:
     """RGBA8 views -> RGB float64 in [0,1] (value / 255)."""
     return rgba8[..., :3].to(torch.float64) / 255.0
+
+
+# ----------------------------------------------------------------------------
+# Serving workload: three rigs filming a scene while moving
+# ----------------------------------------------------------------------------
+
+SERVING_RIGS = ("A", "B", "C")
+
+
+@dataclass
+class ServingRig:
+    """One rig of the serving workload: `keyframes` rendered frames of the rig
+    translated by `step` metres per frame along world x; frame f of the stream
+    shows keyframe `keyframe_of(f)` (a ping-pong walk, so consecutive frames
+    are always one step apart)."""
+    name: str
+    rigs: list              # Rig per keyframe
+    views: list             # (V,H,W,4) uint8 tensor per keyframe
+    labels: torch.Tensor    # (V,H,W) int32, static grid
+    GW: int
+    GH: int
+    params: dict
+    step: float
+
+    @property
+    def V(self) -> int:
+        return self.rigs[0].V
+
+    def keyframe_of(self, f: int) -> int:
+        n = len(self.rigs)
+        if n == 1:
+            return 0
+        m = f % (2 * n - 2)
+        return m if m < n else 2 * n - 2 - m
+
+
+def _translated(rig: Rig, d: np.ndarray) -> Rig:
+    # the camera centres move by d: t' = t - R d
+    t = rig.t - np.einsum("vij,j->vi", rig.R, d)
+    return Rig(rig.K.copy(), rig.R.copy(), t, rig.W, rig.H)
+
+
+def make_serving_rig(name: str, device="cpu", keyframes: int = 4, scale: float = 1.0,
+                     step: float = 0.015) -> ServingRig:
+    """Rig A: 8 x 1024x768 on a 30-degree arc (superpixel pitch 14, perturbed);
+    B: 9 x 1280x720 3x3 grid, baseline 0.08 (pitch 16); C: 16 x 1920x1080 4x4
+    grid, baseline 0.08 (pitch 16).  Depth range [2, 8], 256 labels, 6 cold
+    iterations; each rig films its own seeded scene while translating `step`
+    (<= 2 cm) per frame."""
+    idx = {"A": 51, "B": 52, "C": 53}[name]
+    rng = np.random.default_rng(SCENE_SEED_BASE + idx)
+    if name == "A":
+        W, H = _rnd(1024 * scale), _rnd(768 * scale)
+        f = 300.0 * W / 320.0
+        rig0 = arc_rig(8, 30.0, 5.0, f, W, H)
+        pitch, perturb = 14.0, True
+        scene = _random_scene(rng, 12, 3, 4, f, 2.0, 8.0, 1.6)
+    elif name == "B":
+        W, H = _rnd(1280 * scale), _rnd(720 * scale)
+        f = 300.0 * W / 320.0
+        rig0 = grid_rig(3, 3, 0.08, f, W, H)
+        pitch, perturb = 16.0, False
+        scene = _random_scene(rng, 16, 4, 6, f, 2.0, 8.0, 2.0)
+    elif name == "C":
+        W, H = _rnd(1920 * scale), _rnd(1080 * scale)
+        f = 300.0 * W / 320.0
+        rig0 = grid_rig(4, 4, 0.08, f, W, H)
+        pitch, perturb = 16.0, False
+        scene = _random_scene(rng, 24, 6, 10, f, 2.0, 8.0, 2.2)
+    else:
+        raise ValueError(f"unknown serving rig {name}")
+    rigs, views = [], []
+    for k in range(keyframes):
+        rig = _translated(rig0, np.array([step * k, 0.0, 0.0]))
+        rgb, _, _ = render(rig, scene, device)
+        views.append(quantize_rgba8(rgb))
+        rigs.append(rig)
+        del rgb
+    labs = []
+    GW = GH = None
+    for v in range(rig0.V):
+        lab, GW, GH = grid_labels(W, H, pitch, perturb, seed=SCENE_SEED_BASE + 100 * idx + v)
+        labs.append(lab)
+    labels = torch.from_numpy(np.ascontiguousarray(np.stack(labs))).to(device)
+    params = dict(d_min=2.0, d_max=8.0, num_labels=256, iterations=6,
+                  T=0.04, sigma=0.0, alpha=0.1, eta=0.5, kernel_size_init=0, kernel_step_sp=5.0,
+                  max_neighbor_views=8, depth_domain=0, jitter=1, term_mask=7, sweep_frame=0,
+                  seed=(SCENE_SEED_BASE + idx) ^ 0x5EED, lf_index=0, xy_eps=0.0, warm_iter_offset=0)
+    return ServingRig(name, rigs, views, labels, GW, GH, params, step)

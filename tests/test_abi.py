@@ -100,3 +100,34 @@ def test_host_entry_points_reject_bad_arguments(lfd):
     out = (ctypes.c_int32 * 8)()
     assert lib.lfd_neighbor_views(cams, 1, 0, out, None) == 1          # fewer than 2 views
     assert lib.lfd_kernel_offsets(10, 2, 1, None, 0) == 9 + 8 * 2       # size query
+
+
+def test_workspace_required_counts_every_per_pixel_buffer(lfd):
+    """The HBM figure the budget and the server's admission use: at least the
+    per-pixel buffers (24-B RGBA8 sampling texture, 16-B rasterised map, 4-B
+    superpixel pixel list) and exactly linear in the number of equal views."""
+    lib = lfd.load()
+    lf1 = synth.make_config(1, scale=0.25)
+    def req(V):
+        K, R, t = lf1.rig.K[:1].repeat(V, 0), lf1.rig.R[:1].repeat(V, 0), lf1.rig.t[:1].repeat(V, 0)
+        cams = lfd.make_cameras(K, R, t, lf1.rig.W, lf1.rig.H)
+        gw = (ctypes.c_int32 * V)(*([lf1.GW] * V))
+        gh = (ctypes.c_int32 * V)(*([lf1.GH] * V))
+        lf = lfd.LightFieldC(V, 0, cams, None, None, None, gw, gh)
+        out = ctypes.c_uint64()
+        assert lib.lfd_workspace_required(1, ctypes.byref(lf), ctypes.byref(out)) == 0
+        return out.value
+    px = lf1.rig.W * lf1.rig.H
+    assert req(2) >= 2 * px * (24 + 16 + 4)
+    a, b, c = req(2), req(4), req(8)
+    assert (c - b) >= 2 * (b - a) - 4096 and (c - b) <= 2 * (b - a) + 4096
+    out = ctypes.c_uint64()
+    assert lib.lfd_workspace_required(0, None, ctypes.byref(out)) == 1
+
+
+@pytest.mark.skipif(__import__("torch").cuda.is_available(), reason="checks the no-device path")
+def test_server_create_fails_cleanly_without_a_device(lfd):
+    lib = lfd.load()
+    h = ctypes.c_void_p()
+    assert lib.lfd_server_create(ctypes.byref(h), 0, 0, 2) != 0
+    assert not h.value
