@@ -17,11 +17,14 @@
 //       the pixels whose 3-D point is not behind view i's surface, and O_i
 //       (Eq. 11) = eta (1 - min_j omega) when some pixel lies behind it.
 //
-// Mapping: one warp per superpixel; lanes own pixels (8 per lane in
-// registers, more streamed), so the gathers of a warp into a neighbour view's
+// Mapping: one warp per superpixel; lanes own pixels (ceil(n/32) slots per
+// lane, a compile-time count chosen per superpixel, up to 10 staged in shared
+// memory and more streamed), so the gathers of a warp into a neighbour view's
 // map fall in a compact footprint.  Hypotheses are scored one after another by
 // the whole warp; per view the five sums are reduced with REDUX (counts) and
 // butterfly shuffles (sums) in a fixed order, so results are deterministic.
+// What does not depend on the view (the FP32 form of the plane and E_s) is
+// computed once per candidate, lane-parallel over a batch of 32.
 //
 // Projection precision: for each (hypothesis, view) the homography applied to
 // the superpixel's anchor pixel is composed in FP64 and split into an integer
@@ -36,7 +39,8 @@ namespace lfd {
 typedef double4_32a dbl4;
 
 constexpr int PROP_WARPS = 4;
-constexpr int PM = 8;   // pixels per lane held in registers (256 per warp)
+constexpr int SLOTS_MAX = 10;   // pixel slots per lane staged in shared memory (320 pixels per warp)
+
 
 // ---------------------------------------------------------------------------
 // plane coefficients of a state: g with 1/depth(p) = g . (p,1)
@@ -89,6 +93,11 @@ cudaError_t launch_plane_prep(const Workspace &w, const Consts &c, const float4 
 // ---------------------------------------------------------------------------
 // rasteriser: warp per superpixel writes {colour, depth value} of its pixels
 // ---------------------------------------------------------------------------
+//
+// The map holds the superpixel's mean colour times sqrt(k_col) and the depth
+// value (inverse depth, or depth in the metric domain) times sqrt(k_sig) of
+// the view's light field, so that the exponents of Eq. 7 / Eq. 9 and of the
+// Gaussian of Eq. 10 are plain squared distances in the energy kernel.
 
 __global__ void __launch_bounds__(128) k_rasterize(Workspace w, Consts c, float *const *depth)
 {
@@ -102,6 +111,8 @@ __global__ void __launch_bounds__(128) k_rasterize(Workspace w, Consts c, float 
     const float4 rc = w.sp_rc[gs];
     const float4 col = w.sp_col[gs];
     const int2 ref = w.sp_ref[gs];
+    const float cgain = vd.col_gain, dgain = vd.dep_gain;
+    const float4 cc = make_float4(col.x * cgain, col.y * cgain, col.z * cgain, 0.f);
     float4 *map = vd.map;
     float *dep = depth ? depth[v] : nullptr;
     for (int i = lane; i < n; i += 32) {
@@ -111,7 +122,7 @@ __global__ void __launch_bounds__(128) k_rasterize(Workspace w, Consts c, float 
         const bool ok = rc.w != 0.f && inv > 0.f && isfinite(inv);
         const float dv = ok ? (c.domain == 0 ? inv : 1.0f / inv) : 0.f;
         const long long p = (long long)y * vd.W + x;
-        map[p] = make_float4(col.x, col.y, col.z, dv);
+        map[p] = make_float4(cc.x, cc.y, cc.z, dv * dgain);
         if (dep) dep[p] = ok ? 1.0f / inv : 0.f;
     }
 }
@@ -132,7 +143,9 @@ cudaError_t launch_rasterize(const Workspace &w, const Consts &c, float *const *
 // integer pixel (xa, ya) near the projection of the superpixel's reference
 // pixel under its current plane (composed in FP64, stored in FP32), and for
 // each 8-neighbour its depth, centroid and colour weight.  A hypothesis g is
-// then applied with FP32 arithmetic on small quantities only:
+// reduced once, in FP64, to the FP32 quantities of HypF (E_s of Eq. 5-7
+// included), lane-parallel over the candidates of a batch; the per-pixel work
+// is then FP32 on small quantities only:
 //   dg = g.(ref,1) - g_a.(ref,1)  (FP64 difference, rounded once),
 //   hw = hw_a + q_z dg,   cx = Ex + Dx dg,   cy = Ey + Dy dg,
 //   per pixel offset (du,dv) from ref:
@@ -156,30 +169,43 @@ struct alignas(16) SpNb {
     int ok;
 };
 
+// the superpixel a warp works on (identical in every lane)
+struct WarpSP {
+    int gs, v, s, n, off, nnb, gx, gy;
+    int2 ref;
+    float cr, cg, cb, minw, sum_w;       // colour scaled by sqrt(k_col)
+};
+
 struct alignas(16) SpShared {
-    float2 px[32 * PM];                  // pixel offsets from ref of the first 32*PM pixels
+    float2 px[32 * SLOTS_MAX];           // pixel offsets from ref of the first 32*SLOTS_MAX pixels
+    WarpSP S;
     SpView view[LFD_MAXN];
     SpNb nb[8];
     double cx, cy, rx, ry, rz, rn, grefa;        // centroid, its ray K^-1(c,1), |ray|, anchor g.(ref,1)
     double best_ig;                              // winning candidate (propagation / refinement)
     float bnx, bny, bnz;
     int best_m;
-    float k_col, k_sig, xy_lo, xy_hi, eta;       // energy constants of the superpixel's light field
+    float k_sig, xy_lo, xy_hi, eta;              // energy constants of the superpixel's light field
     int term_mask;
+};
+
+// FP32 reduction of a hypothesis g (see above): gp(p) = g0 du + g1 dv + gr is
+// the hypothesis' inverse depth at pixel p, dgr the anchored offset of
+// g.(ref,1), es its smoothness E_s.
+struct HypF {
+    float g0, g1, gr, dgr, es;
 };
 
 // candidate planes of one 32-wide batch (propagation) or the 8 triangles (refinement)
 struct alignas(16) CandShared {
-    double g0[32], g1[32], g2[32], ig[32];
+    float g0[32], g1[32], gr[32], dgr[32], es[32];
+    double ig[32];
     float nx[32], ny[32], nz[32];
 };
 
-struct WarpSP {
-    int gs, v, s, n, off, nnb, gx, gy;
-    int2 ref;
-    float cr, cg, cb, minw, sum_w;
-    const float2 *px;                    // this warp's pixel offsets (du,dv) in shared memory
-};
+// per-warp records of the 4-warp propagation and score CTAs
+__shared__ SpShared g_sh[PROP_WARPS];
+__shared__ CandShared g_cs[PROP_WARPS];
 
 struct Acc {
     unsigned cnt, nx, ny;
@@ -188,17 +214,70 @@ struct Acc {
 
 struct ViewK {
     float hw, a20, a21, cx, b0, b1, cy, c0, c1, lo_x, hi_x, lo_y, hi_y;
-    float k_col, k_sig, xy;
+    float xy;
     int xa, ya, Wi;
     const float4 *map;
 };
 
+// E_s (Eq. 5-7) of plane g for this lane; neighbours in ring order.
+template <int DOMAIN>
+__device__ __forceinline__ float smoothness(const SpShared &sh, float sum_w, double g0, double g1, double g2)
+{
+    if (!(sum_w > 0.f)) return 1.f;
+    float num = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const SpNb &nb = sh.nb[j];
+        if (!nb.ok) continue;
+        const double ext = g0 * nb.cx + g1 * nb.cy + g2;         // plane's inverse depth at c_j
+        float dl;
+        bool has = true;
+        if (DOMAIN == 0) {
+            dl = (float)(nb.invd - ext);
+        } else {
+            has = ext > 0.0;
+            dl = has ? (float)(nb.d - 1.0 / ext) : 0.f;
+        }
+        if (has) num += nb.w * ex2_approx(-dl * dl * sh.k_sig);
+    }
+    return num / sum_w;
+}
+
+template <int DOMAIN>
+__device__ __forceinline__ HypF hyp_prep(const WarpSP &S, const SpShared &sh, double g0, double g1, double g2)
+{
+    HypF h;
+    const double gref = g0 * S.ref.x + g1 * S.ref.y + g2;
+    h.g0 = (float)g0;
+    h.g1 = (float)g1;
+    h.gr = (float)gref;
+    h.dgr = (float)(gref - sh.grefa);
+    h.es = smoothness<DOMAIN>(sh, S.sum_w, g0, g1, g2);
+    return h;
+}
+
+__device__ __forceinline__ void cand_store(CandShared &cs, int lane, const HypF &h)
+{
+    cs.g0[lane] = h.g0; cs.g1[lane] = h.g1; cs.gr[lane] = h.gr; cs.dgr[lane] = h.dgr; cs.es[lane] = h.es;
+}
+
+__device__ __forceinline__ HypF cand_load(const CandShared &cs, int src)
+{
+    HypF h;
+    h.g0 = cs.g0[src]; h.g1 = cs.g1[src]; h.gr = cs.gr[src]; h.dgr = cs.dgr[src]; h.es = cs.es[src];
+    return h;
+}
+
 // One pixel-view sample of Eq. 9-11, branch-free so that the samples of an
 // unrolled loop keep their gathers in flight together; `act` false (a lane
-// past the superpixel's last pixel) contributes nothing.
+// past the superpixel's last pixel) contributes nothing.  gp: the
+// hypothesis' inverse depth at the pixel.  Map colours and depth values carry
+// sqrt(k_col) and sqrt(k_sig); the homography rows carry 1/sqrt(k_sig)
+// (inverse-depth domain: 1/z_i = gp / Nw comes out scaled) or sqrt(k_sig)
+// (metric: z_i = Nw / gp), which leaves the pixel position fx, fy unchanged.
 template <int DOMAIN>
 __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du, float dv, float gp, float cr,
-                                              float cg, float cb, const Consts &c, Acc &a)
+                                              float cg, float cb, Acc &a)
 {
     const float Nw = fmaf(K.a20, du, fmaf(K.a21, dv, K.hw));     // camera-i depth * g.p
     const float ex = fmaf(K.b0, du, fmaf(K.b1, dv, K.cx));
@@ -212,89 +291,66 @@ __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du
     const int idx = ok ? iy * K.Wi + ix : 0;                     // in-bounds address either way
     const float4 t = __ldg(K.map + idx);
     const float dr = t.x - cr, dg = t.y - cg, db = t.z - cb;
-    const float om = ex2_approx(-fmaf(dr, dr, fmaf(dg, dg, db * db)) * K.k_col);   // Eq. 9 summand
+    const float om = ex2_approx(-fmaf(dr, dr, fmaf(dg, dg, db * db)));   // Eq. 9 summand
     a.cnt += ok ? 1u : 0u;
     a.sw += ok ? om : 0.f;
     const bool has = ok && t.w > 0.f;
     float val;
     bool inX;
     if (DOMAIN == 0) {
-        val = gp * r;                                            // 1 / z_i(P)
+        val = gp * r;                                            // 1 / z_i(P), scaled
         inX = has && val >= t.w * K.xy;
     } else {
-        val = Nw * rcp_approx(gp);                               // z_i(P)
+        val = Nw * rcp_approx(gp);                               // z_i(P), scaled
         inX = has && val <= t.w * K.xy;
     }
     const float dd = val - t.w;
-    const float G = ex2_approx(-dd * dd * K.k_sig);              // Eq. 10 summand
+    const float G = ex2_approx(-dd * dd);                        // Eq. 10 summand
     a.nx += inX ? 1u : 0u;
     a.sg += inX ? G : 0.f;
     a.ny += (has && !inX) ? 1u : 0u;
 }
 
-// E(g) for the warp's superpixel; all lanes return the same value.  When
-// `rec` is non-null lane 0 writes the terms record of lfd_score.
-template <int DOMAIN>
-__device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, const SpShared &sh, double g0,
-                          double g1, double g2, int lane, float *rec)
+// E(h) for the warp's superpixel with SL pixel slots per lane; all lanes
+// return the same value.  Unless MASK_ALL, every slot but the last is full
+// (n > 32 (SL - 1)).  When `rec` is non-null lane 0 writes the terms record
+// of lfd_score.
+template <int DOMAIN, int SL, bool MASK_ALL = false>
+__device__ __noinline__ float evaluate(const Workspace &w, const HypF h, float *rec)
 {
-    const double gref = g0 * S.ref.x + g1 * S.ref.y + g2;
-    const float g0f = (float)g0, g1f = (float)g1, grf = (float)gref;
-    const float dgr = (float)(gref - sh.grefa);
-
-    // ---- smoothness (Eq. 5-7) on lanes 0..7
-    float num = 0.f;
-    if (lane < 8) {
-        const SpNb &nb = sh.nb[lane];
-        if (nb.ok) {
-            const double ext = g0 * nb.cx + g1 * nb.cy + g2;     // plane's inverse depth at c_j
-            float dl;
-            bool has = true;
-            if (DOMAIN == 0) {
-                dl = (float)(nb.invd - ext);
-            } else {
-                has = ext > 0.0;
-                dl = has ? (float)(nb.d - 1.0 / ext) : 0.f;
-            }
-            num = has ? nb.w * ex2_approx(-dl * dl * sh.k_sig) : 0.f;
-        }
-    }
-    num += __shfl_xor_sync(0xffffffffu, num, 4);
-    num += __shfl_xor_sync(0xffffffffu, num, 2);
-    num += __shfl_xor_sync(0xffffffffu, num, 1);
-    num = __shfl_sync(0xffffffffu, num, 0);
-    const float Es = S.sum_w > 0.f ? num / S.sum_w : 1.f;
-
+    const int lane = threadIdx.x & 31;
+    const SpShared &sh = g_sh[threadIdx.x >> 5];
+    const WarpSP S = sh.S;
     float ec = 0.f;
     for (int k = 0; k < S.nnb; k++) {
         const SpView &sv = sh.view[k];
         ViewK K;
-        K.hw = fmaf(sv.qw, dgr, sv.hw_a);
-        K.cx = fmaf(sv.Dx, dgr, sv.Ex);
-        K.cy = fmaf(sv.Dy, dgr, sv.Ey);
-        K.b0 = fmaf(sv.Dx, g0f, sv.Pp00);
-        K.b1 = fmaf(sv.Dx, g1f, sv.Pp01);
-        K.c0 = fmaf(sv.Dy, g0f, sv.Pp10);
-        K.c1 = fmaf(sv.Dy, g1f, sv.Pp11);
-        K.a20 = fmaf(sv.qw, g0f, sv.P20);
-        K.a21 = fmaf(sv.qw, g1f, sv.P21);
+        K.hw = fmaf(sv.qw, h.dgr, sv.hw_a);
+        K.cx = fmaf(sv.Dx, h.dgr, sv.Ex);
+        K.cy = fmaf(sv.Dy, h.dgr, sv.Ey);
+        K.b0 = fmaf(sv.Dx, h.g0, sv.Pp00);
+        K.b1 = fmaf(sv.Dx, h.g1, sv.Pp01);
+        K.c0 = fmaf(sv.Dy, h.g0, sv.Pp10);
+        K.c1 = fmaf(sv.Dy, h.g1, sv.Pp11);
+        K.a20 = fmaf(sv.qw, h.g0, sv.P20);
+        K.a21 = fmaf(sv.qw, h.g1, sv.P21);
         K.lo_x = sv.lo_x; K.hi_x = sv.hi_x; K.lo_y = sv.lo_y; K.hi_y = sv.hi_y;
         K.xa = sv.xa; K.ya = sv.ya; K.Wi = sv.Wi;
         K.map = sv.map;
-        K.k_col = sh.k_col;
-        K.k_sig = sh.k_sig;
         K.xy = DOMAIN == 0 ? sh.xy_lo : sh.xy_hi;
         Acc a = {0u, 0u, 0u, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < PM; j++) {
-            const float2 d = S.px[32 * j + lane];
-            energy_sample<DOMAIN>(K, lane + 32 * j < S.n, d.x, d.y, fmaf(g0f, d.x, fmaf(g1f, d.y, grf)), S.cr, S.cg,
-                                  S.cb, c, a);
+        for (int j = 0; j < SL; j++) {
+            const float2 d = sh.px[32 * j + lane];
+            energy_sample<DOMAIN>(K, (!MASK_ALL && j + 1 < SL) || lane + 32 * j < S.n, d.x, d.y,
+                                  fmaf(h.g0, d.x, fmaf(h.g1, d.y, h.gr)), S.cr, S.cg, S.cb, a);
         }
-        for (int i = 32 * PM + lane; i < S.n; i += 32) {          // pixels beyond the register chunk
-            const unsigned pk = __ldg(w.sp_pix + S.off + i);
-            const float du = (float)((int)(pk & 0xffff) - S.ref.x), dv = (float)((int)(pk >> 16) - S.ref.y);
-            energy_sample<DOMAIN>(K, true, du, dv, fmaf(g0f, du, fmaf(g1f, dv, grf)), S.cr, S.cg, S.cb, c, a);
+        if (SL == SLOTS_MAX) {
+            for (int i = 32 * SL + lane; i < S.n; i += 32) {    // pixels beyond the staged slots
+                const unsigned pk = __ldg(w.sp_pix + S.off + i);
+                const float du = (float)((int)(pk & 0xffff) - S.ref.x), dv = (float)((int)(pk >> 16) - S.ref.y);
+                energy_sample<DOMAIN>(K, true, du, dv, fmaf(h.g0, du, fmaf(h.g1, dv, h.gr)), S.cr, S.cg, S.cb, a);
+            }
         }
         unsigned cnt, nx;
         if (S.n < 65536) {    // counts fit 16 bits: one REDUX for |Omega_i| and |X_i|
@@ -317,9 +373,9 @@ __device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, 
         }
     }
     const float Ec = S.nnb > 0 ? ec / (float)S.nnb : 0.f;                                  // Eq. 8
-    const float E = ((sh.term_mask & 2) ? Ec : 1.f) * ((sh.term_mask & 1) ? Es : 1.f);    // Eq. 3
+    const float E = ((sh.term_mask & 2) ? Ec : 1.f) * ((sh.term_mask & 1) ? h.es : 1.f);  // Eq. 3
     if (rec && lane == 0) {
-        rec[0] = E; rec[1] = Es; rec[2] = Ec;
+        rec[0] = E; rec[1] = h.es; rec[2] = Ec;
     }
     return E;
 }
@@ -327,8 +383,9 @@ __device__ float evaluate(const Workspace &w, const Consts &c, const WarpSP &S, 
 // Warp-wide set-up of a superpixel: registers (pixels, colour) and the warp's
 // shared record.  Returns false for an empty superpixel.  `ga` is the anchor
 // plane (the current plane when valid).
-__device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *planes_in, int gs, int lane, WarpSP &S,
-                         SpShared &sh, bool ga_valid, double ga0, double ga1, double ga2)
+template <int DOMAIN>
+__device__ bool setup_sp(const Workspace &w, const float4 *planes_in, int gs, int lane, WarpSP &S, SpShared &sh,
+                         bool ga_valid, double ga0, double ga1, double ga2)
 {
     S.gs = gs;
     S.v = __ldg(w.sp_view + gs);
@@ -342,7 +399,7 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
     S.gy = S.s / vd.GW;
     S.ref = w.sp_ref[gs];
     const float4 col = w.sp_col[gs];
-    S.cr = col.x; S.cg = col.y; S.cb = col.z; S.minw = col.w;
+    S.minw = col.w;
     const double2 cc = w.sp_cen[gs];
     const double *Ki = vd.Kinv;
     const double rx = Ki[0] * cc.x + Ki[1] * cc.y + Ki[2];
@@ -350,7 +407,6 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
     const double rz = Ki[6] * cc.x + Ki[7] * cc.y + Ki[8];
     const double grefa = ga_valid ? ga0 * S.ref.x + ga1 * S.ref.y + ga2 : 0.5 * (vd.inv_dmin + vd.inv_dmax);
     if (lane == 0) {
-        sh.k_col = vd.k_col;
         sh.k_sig = vd.k_sig;
         sh.xy_lo = vd.xy_lo;
         sh.xy_hi = vd.xy_hi;
@@ -379,7 +435,7 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
                 if (pj.x > 0.f && isfinite(pj.x)) {
                     nb.ok = 1;
                     const float4 cj = w.sp_col[j];
-                    const float dr = cj.x - S.cr, dg = cj.y - S.cg, db = cj.z - S.cb;
+                    const float dr = cj.x - col.x, dg = cj.y - col.y, db = cj.z - col.z;
                     a = fmaf(dr, dr, fmaf(dg, dg, db * db)) * vd.k_col;
                     const double2 c2 = w.sp_cen[j];
                     nb.d = pj.x;
@@ -403,6 +459,8 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
     wgt += __shfl_xor_sync(0xffffffffu, wgt, 2);
     wgt += __shfl_xor_sync(0xffffffffu, wgt, 1);
     S.sum_w = __shfl_sync(0xffffffffu, wgt, 0);
+    const float cgain = vd.col_gain;             // the map colours carry the same factor
+    S.cr = col.x * cgain; S.cg = col.y * cgain; S.cb = col.z * cgain;
 
     // neighbour view k = lane: homography pieces anchored at an integer pixel (FP64 -> FP32)
     if (lane < S.nnb) {
@@ -413,24 +471,27 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
         const double hx = fma(pd.q[0], grefa, pr0), hy = fma(pd.q[1], grefa, pr1), hw = fma(pd.q[2], grefa, pr2);
         double xa = 0.0, ya = 0.0;
         if (hw > 0.0) {
-            xa = floor(hx / hw);
-            ya = floor(hy / hw);
+            const double ihw = 1.0 / hw;
+            xa = floor(hx * ihw);
+            ya = floor(hy * ihw);
             xa = fmin(fmax(xa, -1048576.0), 1048576.0);
             ya = fmin(fmax(ya, -1048576.0), 1048576.0);
         }
+        // rows scaled so that gp / Nw (or Nw / gp) carries sqrt(k_sig), see energy_sample
+        const double rs = DOMAIN == 0 ? 1.0 / (double)vd.dep_gain : (double)vd.dep_gain;
         SpView sv;
-        sv.hw_a = (float)hw;
-        sv.qw = (float)pd.q[2];
-        sv.Ex = (float)(hx - xa * hw);
-        sv.Ey = (float)(hy - ya * hw);
-        sv.Dx = (float)(pd.q[0] - xa * pd.q[2]);
-        sv.Dy = (float)(pd.q[1] - ya * pd.q[2]);
-        sv.Pp00 = (float)(pd.P[0] - xa * pd.P[6]);
-        sv.Pp01 = (float)(pd.P[1] - xa * pd.P[7]);
-        sv.Pp10 = (float)(pd.P[3] - ya * pd.P[6]);
-        sv.Pp11 = (float)(pd.P[4] - ya * pd.P[7]);
-        sv.P20 = (float)pd.P[6];
-        sv.P21 = (float)pd.P[7];
+        sv.hw_a = (float)(hw * rs);
+        sv.qw = (float)(pd.q[2] * rs);
+        sv.Ex = (float)((hx - xa * hw) * rs);
+        sv.Ey = (float)((hy - ya * hw) * rs);
+        sv.Dx = (float)((pd.q[0] - xa * pd.q[2]) * rs);
+        sv.Dy = (float)((pd.q[1] - ya * pd.q[2]) * rs);
+        sv.Pp00 = (float)((pd.P[0] - xa * pd.P[6]) * rs);
+        sv.Pp01 = (float)((pd.P[1] - xa * pd.P[7]) * rs);
+        sv.Pp10 = (float)((pd.P[3] - ya * pd.P[6]) * rs);
+        sv.Pp11 = (float)((pd.P[4] - ya * pd.P[7]) * rs);
+        sv.P20 = (float)(pd.P[6] * rs);
+        sv.P21 = (float)(pd.P[7] * rs);
         sv.xa = (int)xa;
         sv.ya = (int)ya;
         sv.Wi = pd.Wi;
@@ -444,9 +505,9 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
         sh.view[lane] = sv;
     }
 
-    // pixel offsets of the first 32*PM pixels
+    // pixel offsets of the first 32*SLOTS_MAX pixels (zero past the last pixel)
 #pragma unroll
-    for (int j = 0; j < PM; j++) {
+    for (int j = 0; j < SLOTS_MAX; j++) {
         const int i = lane + 32 * j;
         float2 d = make_float2(0.f, 0.f);
         if (i < S.n) {
@@ -455,65 +516,54 @@ __device__ bool setup_sp(const Workspace &w, const Consts &c, const float4 *plan
         }
         sh.px[i] = d;
     }
-    S.px = sh.px;
+    if (lane == 0) sh.S = S;
     __syncwarp();
     return true;
+}
+
+// slots per lane for a superpixel of n pixels (the instantiated counts)
+__device__ __forceinline__ int slot_class(int n)
+{
+    const int s = (n + 31) >> 5;
+    return s <= 1 ? 1 : (s <= 8 ? s : SLOTS_MAX);
 }
 
 // ---------------------------------------------------------------------------
 // propagation + refinement
 // ---------------------------------------------------------------------------
 
-// one Jacobi update of superpixel gs by one warp (iteration `iter`, 1-based)
-template <int DOMAIN>
-__device__ __forceinline__ void propagate_sp(const Workspace &w, const Consts &c, int iter, int gs, int lane,
-                                             SpShared &sh, CandShared &cs, const float4 *planes_in,
-                                             float4 *planes_out, int *choice, float *energy)
+// one Jacobi update of superpixel gs by one warp (iteration `iter`, 1-based),
+// its pixels in SL slots per lane
+template <int DOMAIN, int SL>
+__device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, const float4 *planes_in,
+                                          float4 *planes_out, int *choice, float *energy)
 {
-    {
-        const ViewDev &vd0 = w.views[__ldg(w.sp_view + gs)];
-        if (c.batch_iters && iter > vd0.iters) {   // this light field has finished: carry its plane through
-            if (lane == 0) {
-                planes_out[gs] = planes_in[gs];
-                if (choice) { choice[2 * gs] = 0; choice[2 * gs + 1] = -1; }
-                if (energy) { energy[2 * gs] = -INFINITY; energy[2 * gs + 1] = -INFINITY; }
-            }
-            return;
-        }
-    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    SpShared &sh = g_sh[wid];
+    CandShared &cs = g_cs[wid];
+    const WarpSP S = sh.S;
     const dbl4 gc = w.sp_g[gs];
-    WarpSP S;
-    if (!setup_sp(w, c, planes_in, gs, lane, S, sh, gc.w != 0.0, gc.x, gc.y, gc.z)) {
-        if (lane == 0) {
-            planes_out[gs] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (choice) { choice[2 * gs] = -1; choice[2 * gs + 1] = -1; }
-            if (energy) { energy[2 * gs] = -INFINITY; energy[2 * gs + 1] = -INFINITY; }
-        }
-        return;
-    }
     const ViewDev &vd = w.views[S.v];
     unsigned n_hyp = 0;
-
-    // current plane
     float Ebest = -INFINITY;
-    if (gc.w != 0.0) {
-        Ebest = evaluate<DOMAIN>(w, c, S, sh, gc.x, gc.y, gc.z, lane, nullptr);
-        n_hyp++;
-    }
     if (lane == 0) {
         sh.best_m = 0;
         sh.best_ig = 0.0;
     }
 
-    // propagation step: candidate planes of the kernel (Eq. 4, Fig. 3a)
+    // m = 0: the current plane; m >= 1: the propagation kernel (Eq. 4, Fig. 3a)
     const int ii = min(iter + vd.warm_off, LFD_MAX_ITER_INDEX);
     const int nr = w.radii_cnt[S.v * (LFD_MAX_ITER_INDEX + 1) + ii];
     const short *rad = w.radii + ((long long)S.v * (LFD_MAX_ITER_INDEX + 1) + ii) * LFD_MAX_RADII;
     const int M = 9 + 8 * nr;
-    for (int base = 1; base < M; base += 32) {
+    for (int base = 0; base < M; base += 32) {
         const int m = base + lane;
-        bool ok = m < M;
-        if (ok) {
+        bool ok = false;
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+        if (m == 0) {
+            ok = gc.w != 0.0;
+            g0 = gc.x; g1 = gc.y; g2 = gc.z;
+        } else if (m < M) {
             int dx, dy;
             if (m <= 8) {
                 ring_dir(m - 1, dx, dy);
@@ -525,32 +575,32 @@ __device__ __forceinline__ void propagate_sp(const Workspace &w, const Consts &c
                 dy *= r;
             }
             const int x = S.gx + dx, y = S.gy + dy;
-            ok = x >= 0 && y >= 0 && x < vd.GW && y < vd.GH;
-            if (ok) {
+            if (x >= 0 && y >= 0 && x < vd.GW && y < vd.GH) {
                 const int j = vd.sp_base + y * vd.GW + x;
-                ok = __ldg(w.sp_cnt + j) > 0;
-                if (ok) {
+                if (__ldg(w.sp_cnt + j) > 0) {
                     const dbl4 gj = w.sp_g[j];
                     const double ig = gj.x * sh.cx + gj.y * sh.cy + gj.z;   // candidate's inverse depth at own centroid
                     ok = gj.w != 0.0 && ig > 0.0 && ig >= vd.inv_dmax && ig <= vd.inv_dmin;
                     const float4 pj = planes_in[j];
-                    const double cosr = fabs(pj.y * sh.rx + pj.z * sh.ry + pj.w * sh.rz) / sh.rn;
-                    ok = ok && cosr >= 0.1;                                 // not grazing
-                    cs.g0[lane] = gj.x; cs.g1[lane] = gj.y; cs.g2[lane] = gj.z; cs.ig[lane] = ig;
+                    const double cosr = fabs(pj.y * sh.rx + pj.z * sh.ry + pj.w * sh.rz);
+                    ok = ok && cosr >= 0.1 * sh.rn;                          // not grazing
+                    g0 = gj.x; g1 = gj.y; g2 = gj.z;
+                    cs.ig[lane] = ig;
                     cs.nx[lane] = pj.y; cs.ny[lane] = pj.z; cs.nz[lane] = pj.w;
                 }
             }
         }
+        if (ok) cand_store(cs, lane, hyp_prep<DOMAIN>(S, sh, g0, g1, g2));
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         __syncwarp();
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            const float E = evaluate<DOMAIN>(w, c, S, sh, cs.g0[src], cs.g1[src], cs.g2[src], lane, nullptr);
+            const float E = evaluate<DOMAIN, SL>(w, cand_load(cs, src), nullptr);
             n_hyp++;
             if (E > Ebest) {
                 Ebest = E;
-                if (lane == 0) {
+                if (lane == 0 && base + src > 0) {
                     sh.best_m = base + src;
                     sh.best_ig = cs.ig[src];
                     sh.bnx = cs.nx[src];
@@ -578,17 +628,17 @@ __device__ __forceinline__ void propagate_sp(const Workspace &w, const Consts &c
                 const double e1x = A.Px - P0x, e1y = A.Py - P0y, e1z = A.Pz - P0z;
                 const double e2x = B.Px - P0x, e2y = B.Py - P0y, e2z = B.Pz - P0z;
                 double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-                const double nn = sqrt(nx * nx + ny * ny + nz * nz);
-                const double l1 = sqrt(e1x * e1x + e1y * e1y + e1z * e1z);
-                const double l2 = sqrt(e2x * e2x + e2y * e2y + e2z * e2z);
-                ok = nn > 0.0 && nn >= 1e-12 * l1 * l2;
+                const double nn2 = nx * nx + ny * ny + nz * nz;
+                const double l12 = (e1x * e1x + e1y * e1y + e1z * e1z) * (e2x * e2x + e2y * e2y + e2z * e2z);
+                ok = nn2 > 0.0 && nn2 >= 1e-24 * l12;                     // |n| >= 1e-12 |e1| |e2|
                 if (ok) {
-                    nx /= nn; ny /= nn; nz /= nn;
+                    const double inn = 1.0 / sqrt(nn2);
+                    nx *= inn; ny *= inn; nz *= inn;
                     if (nx * P0x + ny * P0y + nz * P0z > 0.0) { nx = -nx; ny = -ny; nz = -nz; }   // face the camera
-                    ok = fabs(nx * sh.rx + ny * sh.ry + nz * sh.rz) / sh.rn >= 0.1;              // not grazing
+                    ok = fabs(nx * sh.rx + ny * sh.ry + nz * sh.rz) >= 0.1 * sh.rn;              // not grazing
                     double tg0 = 0, tg1 = 0, tg2 = 0;
                     if (ok) ok = plane_to_g(vd, dnew, nx, ny, nz, sh.cx, sh.cy, tg0, tg1, tg2);
-                    cs.g0[lane] = tg0; cs.g1[lane] = tg1; cs.g2[lane] = tg2;
+                    if (ok) cand_store(cs, lane, hyp_prep<DOMAIN>(S, sh, tg0, tg1, tg2));
                     cs.nx[lane] = (float)nx; cs.ny[lane] = (float)ny; cs.nz[lane] = (float)nz;
                 }
             }
@@ -598,7 +648,7 @@ __device__ __forceinline__ void propagate_sp(const Workspace &w, const Consts &c
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            const float E = evaluate<DOMAIN>(w, c, S, sh, cs.g0[src], cs.g1[src], cs.g2[src], lane, nullptr);
+            const float E = evaluate<DOMAIN, SL>(w, cand_load(cs, src), nullptr);
             n_hyp++;
             if (E > Ebest) {
                 Ebest = E;
@@ -622,17 +672,58 @@ __device__ __forceinline__ void propagate_sp(const Workspace &w, const Consts &c
     }
 }
 
+// set-up and slot-count dispatch of one superpixel; each slot count is a
+// separate (not inlined) function, so that every variant gets its own
+// register allocation
+template <int DOMAIN>
+__device__ __forceinline__ void propagate_one(const Workspace &w, const Consts &c, int iter, int gs, int lane,
+                                              const float4 *planes_in, float4 *planes_out, int *choice,
+                                              float *energy)
+{
+    SpShared &sh = g_sh[threadIdx.x >> 5];
+    {
+        const ViewDev &vd0 = w.views[__ldg(w.sp_view + gs)];
+        if (c.batch_iters && iter > vd0.iters) {   // this light field has finished: carry its plane through
+            if (lane == 0) {
+                planes_out[gs] = planes_in[gs];
+                if (choice) { choice[2 * gs] = 0; choice[2 * gs + 1] = -1; }
+                if (energy) { energy[2 * gs] = -INFINITY; energy[2 * gs + 1] = -INFINITY; }
+            }
+            return;
+        }
+    }
+    const dbl4 gc = w.sp_g[gs];
+    WarpSP S;
+    if (!setup_sp<DOMAIN>(w, planes_in, gs, lane, S, sh, gc.w != 0.0, gc.x, gc.y, gc.z)) {
+        if (lane == 0) {
+            planes_out[gs] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (choice) { choice[2 * gs] = -1; choice[2 * gs + 1] = -1; }
+            if (energy) { energy[2 * gs] = -INFINITY; energy[2 * gs + 1] = -INFINITY; }
+        }
+        return;
+    }
+    switch (slot_class(S.n)) {
+    case 1: propagate_sp<DOMAIN, 1>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 2: propagate_sp<DOMAIN, 2>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 3: propagate_sp<DOMAIN, 3>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 4: propagate_sp<DOMAIN, 4>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 5: propagate_sp<DOMAIN, 5>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 6: propagate_sp<DOMAIN, 6>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 7: propagate_sp<DOMAIN, 7>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 8: propagate_sp<DOMAIN, 8>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    default: propagate_sp<DOMAIN, SLOTS_MAX>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    }
+}
+
 template <int DOMAIN, int MINB>
 __global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate(Workspace w, Consts c, int iter,
                                                                      const float4 *planes_in, float4 *planes_out,
                                                                      int *choice, float *energy)
 {
-    __shared__ SpShared shm[PROP_WARPS];
-    __shared__ CandShared cshm[PROP_WARPS];
-    const int wid = threadIdx.x >> 5;
-    const int gs = blockIdx.x * PROP_WARPS + wid;
-    if (gs >= w.S_total) return;
-    propagate_sp<DOMAIN>(w, c, iter, gs, threadIdx.x & 31, shm[wid], cshm[wid], planes_in, planes_out, choice, energy);
+    const int item = blockIdx.x * PROP_WARPS + (threadIdx.x >> 5);
+    if (item >= w.S_total) return;
+    propagate_one<DOMAIN>(w, c, iter, __ldg(w.order + item), threadIdx.x & 31, planes_in, planes_out, choice,
+                          energy);
 }
 
 // persistent warps: superpixels taken from the cost-ordered queue, most expensive first
@@ -642,16 +733,13 @@ __global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate_persistent(
                                                                                 float4 *planes_out, int *choice,
                                                                                 float *energy)
 {
-    __shared__ SpShared shm[PROP_WARPS];
-    __shared__ CandShared cshm[PROP_WARPS];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(&w.queue[1], 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= w.S_total) break;
-        propagate_sp<DOMAIN>(w, c, iter, __ldg(w.order + item), lane, shm[wid], cshm[wid], planes_in, planes_out,
-                             choice, energy);
+        propagate_one<DOMAIN>(w, c, iter, __ldg(w.order + item), lane, planes_in, planes_out, choice, energy);
         __syncwarp();
     }
 }
@@ -707,8 +795,7 @@ __global__ void __launch_bounds__(128) k_score(Workspace w, Consts c, const floa
     if (lane + 32 < LFD_TERMS_STRIDE) rec[lane + 32] = 0.f;
     __syncwarp();
     const int gs = w.views[Q.view].sp_base + Q.sp;
-    __shared__ SpShared shm[4];
-    SpShared &sh = shm[threadIdx.x >> 5];
+    SpShared &sh = g_sh[threadIdx.x >> 5];
     const ViewDev &vd = w.views[Q.view];
     double g0, g1, g2;
     bool okp = false;
@@ -722,9 +809,10 @@ __global__ void __launch_bounds__(128) k_score(Workspace w, Consts c, const floa
     }
     const dbl4 gc = w.sp_g[gs];
     WarpSP S;
-    setup_sp(w, c, planes_state, gs, lane, S, sh, gc.w != 0.0, gc.x, gc.y, gc.z);
+    setup_sp<DOMAIN>(w, planes_state, gs, lane, S, sh, gc.w != 0.0, gc.x, gc.y, gc.z);
     __syncwarp();
-    evaluate<DOMAIN>(w, c, S, sh, g0, g1, g2, lane, rec);
+    const HypF h = hyp_prep<DOMAIN>(S, sh, g0, g1, g2);
+    evaluate<DOMAIN, SLOTS_MAX, true>(w, h, rec);
     // truncated SSD sum of Eq. 2 for this plane (lanes over pixels)
     const double gref = g0 * S.ref.x + g1 * S.ref.y + g2;
     float tsum = 0.f;

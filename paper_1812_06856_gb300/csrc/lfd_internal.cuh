@@ -54,7 +54,8 @@ struct ViewDev {
     float k_sig;             // log2(e) / (2 sigma^2)     (Eq. 6, Eq. 10)
     float eta;               // Eq. 11
     float xy_lo, xy_hi;      // X/Y split: inverse domain X iff zeta >= D xy_lo; depth domain X iff z <= D xy_hi
-    float pad3, pad4;
+    float col_gain;          // sqrt(k_col): scale of the colours in the rasterised maps
+    float dep_gain;          // sqrt(k_sig): scale of their depth values
 };
 
 // view v -> its k-th neighbour view i.  The plane with inverse-depth vector g
