@@ -232,7 +232,7 @@ lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const 
 /* ---- batched frames --------------------------------------------------- */
 
 /* Launch options of lfd_estimate_batch (lfd_batch_options_default fills
- * autotune 0, graph 0, sweep_threads 256, sweep_persistent 0, prop_blocks 7,
+ * autotune 0, graph 0, sweep_threads 256, sweep_persistent 0, prop_blocks 8,
  * prop_persistent 0). */
 typedef struct {
     int32_t autotune;          /* 1: the first call with a new argument signature times the
@@ -247,7 +247,7 @@ typedef struct {
     int32_t sweep_threads;     /* 128 or 256 (0 = 256): labels scored in parallel per superpixel */
     int32_t sweep_persistent;  /* 1: persistent sweep CTAs take superpixels from a queue ordered
                                   by cost (pixels x neighbour views), most expensive first */
-    int32_t prop_blocks;       /* 7 or 8 (0 = 7) resident propagation CTAs per SM */
+    int32_t prop_blocks;       /* 7 or 8 (0 = 8) resident propagation CTAs per SM */
     int32_t prop_persistent;   /* 1: persistent propagation warps over the same ordered queue */
     int32_t reserved[2];       /* must be 0 */
 } lfd_batch_options;

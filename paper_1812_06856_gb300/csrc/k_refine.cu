@@ -199,6 +199,7 @@ struct HypF {
 // candidate planes of one 32-wide batch (propagation) or the 8 triangles (refinement)
 struct alignas(16) CandShared {
     float g0[32], g1[32], gr[32], dgr[32], es[32];
+    float ec[32];                        // running sum over views of V_i + O_i (Eq. 8)
     double ig[32];
     float nx[32], ny[32], nz[32];
 };
@@ -311,73 +312,88 @@ __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du
     a.ny += (has && !inX) ? 1u : 0u;
 }
 
-// E(h) for the warp's superpixel with SL pixel slots per lane; all lanes
-// return the same value.  Unless MASK_ALL, every slot but the last is full
-// (n > 32 (SL - 1)).  When `rec` is non-null lane 0 writes the terms record
-// of lfd_score.
+// The view terms V_i + O_i (Eq. 9-11) of every candidate of `mask` (a batch
+// held in the warp's CandShared), added to cs.ec[candidate] in view order.
+// The loop runs view-outer, candidate-inner: the candidates of one batch
+// project the superpixel to nearly the same region of a neighbour view, so
+// that region's map texels are reused from L1 across the batch.  SL pixel
+// slots per lane; unless MASK_ALL, every slot but the last is full
+// (n > 32 (SL - 1)).  With `rec` (one candidate), lane 0 writes the per-view
+// terms of lfd_score.
 template <int DOMAIN, int SL, bool MASK_ALL = false>
-__device__ __noinline__ float evaluate(const Workspace &w, const HypF h, float *rec)
+__device__ __noinline__ void view_terms(const Workspace &w, unsigned mask, float *rec)
 {
     const int lane = threadIdx.x & 31;
     const SpShared &sh = g_sh[threadIdx.x >> 5];
+    CandShared &cs = g_cs[threadIdx.x >> 5];
     const WarpSP S = sh.S;
-    float ec = 0.f;
     for (int k = 0; k < S.nnb; k++) {
         const SpView &sv = sh.view[k];
-        ViewK K;
-        K.hw = fmaf(sv.qw, h.dgr, sv.hw_a);
-        K.cx = fmaf(sv.Dx, h.dgr, sv.Ex);
-        K.cy = fmaf(sv.Dy, h.dgr, sv.Ey);
-        K.b0 = fmaf(sv.Dx, h.g0, sv.Pp00);
-        K.b1 = fmaf(sv.Dx, h.g1, sv.Pp01);
-        K.c0 = fmaf(sv.Dy, h.g0, sv.Pp10);
-        K.c1 = fmaf(sv.Dy, h.g1, sv.Pp11);
-        K.a20 = fmaf(sv.qw, h.g0, sv.P20);
-        K.a21 = fmaf(sv.qw, h.g1, sv.P21);
-        K.lo_x = sv.lo_x; K.hi_x = sv.hi_x; K.lo_y = sv.lo_y; K.hi_y = sv.hi_y;
-        K.xa = sv.xa; K.ya = sv.ya; K.Wi = sv.Wi;
-        K.map = sv.map;
-        K.xy = DOMAIN == 0 ? sh.xy_lo : sh.xy_hi;
-        Acc a = {0u, 0u, 0u, 0.f, 0.f};
+        unsigned mm = mask;
+        while (mm) {
+            const int src = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const HypF h = cand_load(cs, src);
+            ViewK K;
+            K.hw = fmaf(sv.qw, h.dgr, sv.hw_a);
+            K.cx = fmaf(sv.Dx, h.dgr, sv.Ex);
+            K.cy = fmaf(sv.Dy, h.dgr, sv.Ey);
+            K.b0 = fmaf(sv.Dx, h.g0, sv.Pp00);
+            K.b1 = fmaf(sv.Dx, h.g1, sv.Pp01);
+            K.c0 = fmaf(sv.Dy, h.g0, sv.Pp10);
+            K.c1 = fmaf(sv.Dy, h.g1, sv.Pp11);
+            K.a20 = fmaf(sv.qw, h.g0, sv.P20);
+            K.a21 = fmaf(sv.qw, h.g1, sv.P21);
+            K.lo_x = sv.lo_x; K.hi_x = sv.hi_x; K.lo_y = sv.lo_y; K.hi_y = sv.hi_y;
+            K.xa = sv.xa; K.ya = sv.ya; K.Wi = sv.Wi;
+            K.map = sv.map;
+            K.xy = DOMAIN == 0 ? sh.xy_lo : sh.xy_hi;
+            Acc a = {0u, 0u, 0u, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < SL; j++) {
-            const float2 d = sh.px[32 * j + lane];
-            energy_sample<DOMAIN>(K, (!MASK_ALL && j + 1 < SL) || lane + 32 * j < S.n, d.x, d.y,
-                                  fmaf(h.g0, d.x, fmaf(h.g1, d.y, h.gr)), S.cr, S.cg, S.cb, a);
-        }
-        if (SL == SLOTS_MAX) {
-            for (int i = 32 * SL + lane; i < S.n; i += 32) {    // pixels beyond the staged slots
-                const unsigned pk = __ldg(w.sp_pix + S.off + i);
-                const float du = (float)((int)(pk & 0xffff) - S.ref.x), dv = (float)((int)(pk >> 16) - S.ref.y);
-                energy_sample<DOMAIN>(K, true, du, dv, fmaf(h.g0, du, fmaf(h.g1, dv, h.gr)), S.cr, S.cg, S.cb, a);
+            for (int j = 0; j < SL; j++) {
+                const float2 d = sh.px[32 * j + lane];
+                energy_sample<DOMAIN>(K, (!MASK_ALL && j + 1 < SL) || lane + 32 * j < S.n, d.x, d.y,
+                                      fmaf(h.g0, d.x, fmaf(h.g1, d.y, h.gr)), S.cr, S.cg, S.cb, a);
+            }
+            if (SL == SLOTS_MAX) {
+                for (int i = 32 * SL + lane; i < S.n; i += 32) {    // pixels beyond the staged slots
+                    const unsigned pk = __ldg(w.sp_pix + S.off + i);
+                    const float du = (float)((int)(pk & 0xffff) - S.ref.x), dv = (float)((int)(pk >> 16) - S.ref.y);
+                    energy_sample<DOMAIN>(K, true, du, dv, fmaf(h.g0, du, fmaf(h.g1, dv, h.gr)), S.cr, S.cg, S.cb,
+                                          a);
+                }
+            }
+            unsigned cnt, nx;
+            if (S.n < 65536) {    // counts fit 16 bits: one REDUX for |Omega_i| and |X_i|
+                const unsigned cx2 = __reduce_add_sync(0xffffffffu, a.cnt | (a.nx << 16));
+                cnt = cx2 & 0xffffu;
+                nx = cx2 >> 16;
+            } else {
+                cnt = __reduce_add_sync(0xffffffffu, a.cnt);
+                nx = __reduce_add_sync(0xffffffffu, a.nx);
+            }
+            const unsigned ny = __reduce_add_sync(0xffffffffu, a.ny);
+            const float sw = warp_sum(a.sw), sg = warp_sum(a.sg);
+            const float Si = cnt > 0 ? sw * rcp_approx((float)cnt) : 0.f;                      // Eq. 9
+            const float Vi = (cnt > 0 && nx > 0) ? Si * (sg * rcp_approx((float)nx)) : 0.f;    // Eq. 10
+            const float Oi = (ny > 0 && (sh.term_mask & 4)) ? sh.eta * (1.f - S.minw) : 0.f;   // Eq. 11
+            if (lane == 0) {
+                cs.ec[src] += Vi + Oi;
+                if (rec) {
+                    float *r = rec + LFD_TERMS_HEAD + k * LFD_TERMS_PER_VIEW;
+                    r[0] = Si; r[1] = Vi; r[2] = Oi; r[3] = (float)cnt; r[4] = (float)nx; r[5] = (float)ny;
+                }
             }
         }
-        unsigned cnt, nx;
-        if (S.n < 65536) {    // counts fit 16 bits: one REDUX for |Omega_i| and |X_i|
-            const unsigned cx2 = __reduce_add_sync(0xffffffffu, a.cnt | (a.nx << 16));
-            cnt = cx2 & 0xffffu;
-            nx = cx2 >> 16;
-        } else {
-            cnt = __reduce_add_sync(0xffffffffu, a.cnt);
-            nx = __reduce_add_sync(0xffffffffu, a.nx);
-        }
-        const unsigned ny = __reduce_add_sync(0xffffffffu, a.ny);
-        const float sw = warp_sum(a.sw), sg = warp_sum(a.sg);
-        const float Si = cnt > 0 ? sw * rcp_approx((float)cnt) : 0.f;                      // Eq. 9
-        const float Vi = (cnt > 0 && nx > 0) ? Si * (sg * rcp_approx((float)nx)) : 0.f;    // Eq. 10
-        const float Oi = (ny > 0 && (sh.term_mask & 4)) ? sh.eta * (1.f - S.minw) : 0.f;   // Eq. 11
-        ec += Vi + Oi;
-        if (rec && lane == 0) {
-            float *r = rec + LFD_TERMS_HEAD + k * LFD_TERMS_PER_VIEW;
-            r[0] = Si; r[1] = Vi; r[2] = Oi; r[3] = (float)cnt; r[4] = (float)nx; r[5] = (float)ny;
-        }
     }
-    const float Ec = S.nnb > 0 ? ec / (float)S.nnb : 0.f;                                  // Eq. 8
-    const float E = ((sh.term_mask & 2) ? Ec : 1.f) * ((sh.term_mask & 1) ? h.es : 1.f);  // Eq. 3
-    if (rec && lane == 0) {
-        rec[0] = E; rec[1] = h.es; rec[2] = Ec;
-    }
-    return E;
+    __syncwarp();
+}
+
+// E = E_c E_s (Eq. 3, Eq. 8) of candidate src after view_terms
+__device__ __forceinline__ float cand_energy(const SpShared &sh, const CandShared &cs, int nnb, int src)
+{
+    const float Ec = nnb > 0 ? cs.ec[src] / (float)nnb : 0.f;
+    return ((sh.term_mask & 2) ? Ec : 1.f) * ((sh.term_mask & 1) ? cs.es[src] : 1.f);
 }
 
 // Warp-wide set-up of a superpixel: registers (pixels, colour) and the warp's
@@ -591,12 +607,14 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
             }
         }
         if (ok) cand_store(cs, lane, hyp_prep<DOMAIN>(S, sh, g0, g1, g2));
+        cs.ec[lane] = 0.f;
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         __syncwarp();
+        if (mask) view_terms<DOMAIN, SL>(w, mask, nullptr);
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            const float E = evaluate<DOMAIN, SL>(w, cand_load(cs, src), nullptr);
+            const float E = cand_energy(sh, cs, S.nnb, src);
             n_hyp++;
             if (E > Ebest) {
                 Ebest = E;
@@ -643,12 +661,14 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
                 }
             }
         }
+        cs.ec[lane] = 0.f;
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         __syncwarp();
+        if (mask) view_terms<DOMAIN, SL>(w, mask, nullptr);
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            const float E = evaluate<DOMAIN, SL>(w, cand_load(cs, src), nullptr);
+            const float E = cand_energy(sh, cs, S.nnb, src);
             n_hyp++;
             if (E > Ebest) {
                 Ebest = E;
@@ -811,8 +831,17 @@ __global__ void __launch_bounds__(128) k_score(Workspace w, Consts c, const floa
     WarpSP S;
     setup_sp<DOMAIN>(w, planes_state, gs, lane, S, sh, gc.w != 0.0, gc.x, gc.y, gc.z);
     __syncwarp();
-    const HypF h = hyp_prep<DOMAIN>(S, sh, g0, g1, g2);
-    evaluate<DOMAIN, SLOTS_MAX, true>(w, h, rec);
+    CandShared &cs = g_cs[threadIdx.x >> 5];
+    if (lane == 0) {
+        cand_store(cs, 0, hyp_prep<DOMAIN>(S, sh, g0, g1, g2));
+        cs.ec[0] = 0.f;
+    }
+    __syncwarp();
+    view_terms<DOMAIN, SLOTS_MAX, true>(w, 1u, rec);
+    if (lane == 0) {
+        const float E = cand_energy(sh, cs, S.nnb, 0);
+        rec[0] = E; rec[1] = cs.es[0]; rec[2] = S.nnb > 0 ? cs.ec[0] / (float)S.nnb : 0.f;
+    }
     // truncated SSD sum of Eq. 2 for this plane (lanes over pixels)
     const double gref = g0 * S.ref.x + g1 * S.ref.y + g2;
     float tsum = 0.f;

@@ -182,7 +182,7 @@ struct lfd_ctx {
     std::vector<LfInfo> lfs;
     std::vector<int> nbr;          // [V_total * 8] global view indices
     int fmt = 0;
-    LaunchCfg lc{256, 0, 7, 0, 0};
+    LaunchCfg lc{256, 0, 8, 0, 0};
     // workspace
     Arena ws;
     Workspace w{};
@@ -964,7 +964,7 @@ lfd_status apply_options(lfd_ctx *ctx, const lfd_batch_options &o)
     if (o.autotune) return LFD_OK;
     ctx->lc.sweep_threads = o.sweep_threads ? o.sweep_threads : 256;
     ctx->lc.sweep_persistent = o.sweep_persistent;
-    ctx->lc.prop_blocks = o.prop_blocks ? o.prop_blocks : 7;
+    ctx->lc.prop_blocks = o.prop_blocks ? o.prop_blocks : 8;
     ctx->lc.prop_persistent = o.prop_persistent;
     return LFD_OK;
 }
@@ -1035,7 +1035,7 @@ void lfd_batch_options_default(lfd_batch_options *o)
     if (!o) return;
     memset(o, 0, sizeof(*o));
     o->sweep_threads = 256;
-    o->prop_blocks = 7;
+    o->prop_blocks = 8;
 }
 
 lfd_status lfd_create(lfd_ctx **out, int32_t device, uint64_t hbm_budget_bytes)
