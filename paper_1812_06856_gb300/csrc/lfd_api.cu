@@ -182,7 +182,7 @@ struct lfd_ctx {
     std::vector<LfInfo> lfs;
     std::vector<int> nbr;          // [V_total * 8] global view indices
     int fmt = 0;
-    LaunchCfg lc{256, 0, 8, 0, 0};
+    LaunchCfg lc{256, 0, 8, 1, 0};
     // workspace
     Arena ws;
     Workspace w{};
@@ -1036,6 +1036,7 @@ void lfd_batch_options_default(lfd_batch_options *o)
     memset(o, 0, sizeof(*o));
     o->sweep_threads = 256;
     o->prop_blocks = 8;
+    o->prop_persistent = 1;
 }
 
 lfd_status lfd_create(lfd_ctx **out, int32_t device, uint64_t hbm_budget_bytes)

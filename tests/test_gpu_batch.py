@@ -77,7 +77,7 @@ def test_batch_equals_separate_calls(lfd, two_rigs):
     dict(sweep_threads=128),
     dict(sweep_persistent=1),
     dict(prop_blocks=7),
-    dict(prop_persistent=1),
+    dict(prop_persistent=0),
     dict(sweep_threads=128, sweep_persistent=1, prop_blocks=7, prop_persistent=1),
 ])
 def test_launch_shapes_give_identical_bits(lfd, two_rigs, opt):
