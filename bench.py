@@ -203,12 +203,18 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_1812_06856_gb300 import synth
-    lf = synth.make_config(args.config, device="cpu")
-    if args.config == 3:
-        views = synth.to_rgba_float(lf.rgb, torch.float16)
+    if args.config == 4:         # sampled from light field 0 of the batch
+        m0 = synth.make_mix(1, "cpu", scale=args.scale)[0]
+        views, params = m0.views, m0.params
+        lf = synth.LightField("mix-0", m0.rig, None, oracle_views_rgb(views), None, None, m0.labels.numpy(),
+                              m0.GW, m0.GH, m0.params, m0.pitch)
     else:
-        views = synth.quantize_rgba8(lf.rgb)
-    params = synth.method_params(lf)
+        lf = synth.make_config(args.config, device="cpu")
+        if args.config == 3:
+            views = synth.to_rgba_float(lf.rgb, torch.float16)
+        else:
+            views = synth.quantize_rgba8(lf.rgb)
+        params = synth.method_params(lf)
     cores = host_cores()
     o = make_oracle(lf, views, params, cores)
     rng = np.random.default_rng(99)
@@ -226,7 +232,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.config, lf), "sample": sample},
+            "config": {"workload": mix_workload_name(args.mix, args.scale) if args.config == 4
+                       else workload_name(args.config, lf), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -377,6 +384,155 @@ def run_ours(args):
 
 
 
+def mix_workload_name(n: int, scale: float) -> str:
+    from paper_1812_06856_gb300 import synth
+    shapes = synth.mix_shapes(n, scale)
+    views = sum(s[0] for s in shapes)
+    px = sum(s[0] * s[1] * s[2] for s in shapes)
+    return (f"config 4 (batched): {n} light fields in one lfd_estimate_batch call, {views} views "
+            f"({px / 1e6:.0f} Mpx RGBA8), 4-16 cameras, 640x480..1920x1080, perturbed superpixel grids of "
+            f"pitch 8-32 px, 128-256 labels, 6 iterations")
+
+
+def run_ours_batch(args):
+    """Config 4: one step = one lfd_estimate_batch call over all light fields."""
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    from paper_1812_06856_gb300 import lfd, synth
+    t_gen = time.perf_counter()
+    mix = synth.make_mix(args.mix, dev, scale=args.scale)
+    t_gen = time.perf_counter() - t_gen
+    items = [m.item() for m in mix]
+    ctx = lfd.Context(local)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    out = None
+    for _ in range(max(args.warmup, 1)):
+        flush.fill_(1)
+        out = ctx.estimate_batch(items, out=out)
+    ctx.synchronize()
+    hyp_step, samples_step = ctx.counters()
+    ctx.profile_read()
+    ctx.profile_enable(True)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        ctx.estimate_batch(items, out=out)
+        ev[k][1].record(stream)
+    barrier()
+    clock_info = clocks.stop()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    stage_ms = {k: v[0] / args.steps for k, v in prof.items()}
+    stage_launches = {k: v[1] / args.steps for k, v in prof.items()}
+    sweep_samples = sum(int(m.params["num_labels"]) * m.rig.V * m.rig.W * m.rig.H * min(m.rig.V - 1, 8)
+                        for m in mix)
+    prop_samples = samples_step - sweep_samples
+    dom = max(("sweep", "propagate"), key=lambda k: stage_ms[k])
+    dom_samples = sweep_samples if dom == "sweep" else prop_samples
+    launches = max(stage_launches[dom], 1)
+    avg_launch_ms = stage_ms[dom] / launches
+    achieved = FLOPS_PER_SAMPLE[dom] * dom_samples / launches / (avg_launch_ms / 1000.0) / 1e12
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(f"k_{dom}", f"config4@{args.scale:g}"),
+                "traffic_unit": "DRAM bytes per launch (ncu, profiles/dram_traffic.txt)",
+                "peak_note": f"FP32 FMA peak {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                             f"{sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
+                "algorithmic": f"{FLOPS_PER_SAMPLE[dom]} FP32 flop per pixel-view sample x "
+                               f"{dom_samples / launches:.4g} samples per launch",
+                "avg_launch_ms": avg_launch_ms}
+    line = {"metric": METRIC, "value": hyp_step * ws / (ms / 1000.0), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": mix_workload_name(len(mix), args.scale),
+                       "superpixels": int(sum(m.rig.V * m.GW * m.GH for m in mix)),
+                       "l2": "flushed between steps (256 MiB write)",
+                       "inputs": "device-resident", "parallelism": f"replicas x{ws}"},
+            "samples_per_s": samples_step * ws / (ms / 1000.0), "hypotheses_per_step": hyp_step,
+            "samples_per_step": samples_step, "stage_ms": stage_ms,
+            "gpu_launches": int(sum(v[1] for v in prof.values())), "launch_config": ctx.launch_config(),
+            "roofline": roofline, "clocks": clock_info, "input_generation_s": t_gen}
+    if not args.no_e2e:
+        # end to end: inputs from pinned host memory, planes and depth maps back to host
+        vh = [m.views.cpu().pin_memory() for m in mix]
+        lh = [m.labels.cpu().pin_memory() for m in mix]
+        ph = torch.empty(out[0].shape, dtype=torch.float32).pin_memory()
+        dh = [torch.empty(d.shape, dtype=torch.float32).pin_memory() for d in out[1]]
+
+        def e2e_step():
+            for m, a, b in zip(mix, vh, lh):
+                m.views.copy_(a, non_blocking=True)
+                m.labels.copy_(b, non_blocking=True)
+            ctx.estimate_batch(items, out=out)
+            ph.copy_(out[0], non_blocking=True)
+            for a, b in zip(dh, out[1]):
+                a.copy_(b, non_blocking=True)
+
+        for _ in range(max(args.warmup, 1)):
+            e2e_step()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            evs[k][0].record(stream)
+            e2e_step()
+            evs[k][1].record(stream)
+        barrier()
+        e_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        line["e2e"] = {"value": hyp_step * ws / (e_ms / 1000.0), "unit": UNIT,
+                       "h2d_bytes_per_step": int(sum(a.numel() for a in vh) + 4 * sum(b.numel() for b in lh)),
+                       "d2h_bytes_per_step": int(4 * ph.numel() + 4 * sum(a.numel() for a in dh)),
+                       "ms_per_step": e_ms}
+    if rank == 0 and not args.no_cpu_baseline:
+        m0 = mix[0]
+        lf0 = synth.LightField("mix-0", m0.rig, None, oracle_views_rgb(m0.views), None, None,
+                               m0.labels.cpu().numpy(), m0.GW, m0.GH, m0.params, m0.pitch)
+        cores = host_cores()
+        from oracle import oracle as orc
+        orc.build()
+        o = orc.Oracle(*synth.oracle_inputs(lf0), m0.params, threads=cores)
+        rng = np.random.default_rng(1234)
+        n = max(cores, int(round(args.cpu_sample * o.S_total)))
+        sample_items = np.sort(rng.choice(o.S_total, size=n, replace=False)).astype(np.int32)
+        h, dt = oracle_sample_step(o, m0.params, sample_items)
+        line["cpu_baseline"] = {"value": h / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"light field 0 of the batch ({m0.rig.V} views {m0.rig.W}x{m0.rig.H}): "
+                                          f"{n} of {o.S_total} superpixels, their sweep and refinement "
+                                          f"iteration 1, {h} hypotheses in {dt:.1f} s, FP64 oracle"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def _percentile(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if xs else None
 
@@ -494,7 +650,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
+                    help="1-3: one light field per step; 4: the batched mix of --mix light fields")
+    ap.add_argument("--mix", type=int, default=64, help="light fields of config 4")
     ap.add_argument("--scale", type=float, default=1.0, help="resolution scale (small cases for profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -513,6 +671,8 @@ def main():
         run_serving(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.config == 4:
+        run_ours_batch(args)
     else:
         run_ours(args)
 

@@ -356,6 +356,7 @@ __device__ __noinline__ void view_terms(const Workspace &w, unsigned mask, float
                                       fmaf(h.g0, d.x, fmaf(h.g1, d.y, h.gr)), S.cr, S.cg, S.cb, a);
             }
             if (SL == SLOTS_MAX) {
+#pragma unroll 2
                 for (int i = 32 * SL + lane; i < S.n; i += 32) {    // pixels beyond the staged slots
                     const unsigned pk = __ldg(w.sp_pix + S.off + i);
                     const float du = (float)((int)(pk & 0xffff) - S.ref.x), dv = (float)((int)(pk >> 16) - S.ref.y);

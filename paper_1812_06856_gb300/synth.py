@@ -646,3 +646,106 @@ def make_serving_rig(name: str, device="cpu", keyframes: int = 4, scale: float =
                   max_neighbor_views=8, depth_domain=0, jitter=1, term_mask=7, sweep_frame=0,
                   seed=(SCENE_SEED_BASE + idx) ^ 0x5EED, lf_index=0, xy_eps=0.0, warm_iter_offset=0)
     return ServingRig(name, rigs, views, labels, GW, GH, params, step)
+
+
+# ----------------------------------------------------------------------------
+# Batched workload: many independent light fields of uneven shapes
+# ----------------------------------------------------------------------------
+
+MIX_RESOLUTIONS = ((640, 480), (1024, 768), (1280, 720), (1920, 1080))
+
+
+def grid_labels_fast(W: int, H: int, pitch: float, perturb: bool = False, seed: int = 0, device="cpu"):
+    """grid_labels computed with batched torch.searchsorted (same RNG draws, same
+    result); returns a (H, W) int32 tensor on `device`, GW, GH."""
+    GW = max(1, _rnd(W / pitch))
+    GH = max(1, _rnd(H / pitch))
+    bx = torch.tensor([_rnd(k * W / GW) for k in range(GW + 1)], dtype=torch.int64, device=device)
+    by = torch.tensor([_rnd(k * H / GH) for k in range(GH + 1)], dtype=torch.int64, device=device)
+    u = torch.arange(W, dtype=torch.int64, device=device)
+    v = torch.arange(H, dtype=torch.int64, device=device)
+    gx0 = torch.searchsorted(bx, u, right=True) - 1
+    if not perturb:
+        gy0 = torch.searchsorted(by, v, right=True) - 1
+        return (gy0[:, None] * GW + gx0[None, :]).to(torch.int32), GW, GH
+    rng = np.random.default_rng(seed)
+    m = int(math.floor(pitch / 4))
+    sx = rng.integers(-m, m + 1, size=(GH, GW + 1))
+    sy = rng.integers(-m, m + 1, size=(GW, GH + 1))
+    sx[:, 0] = 0
+    sx[:, GW] = 0
+    sy[:, 0] = 0
+    sy[:, GH] = 0
+    byp = by[None, :] + torch.from_numpy(sy).to(device)                # (GW, GH+1) per column cell
+    gyc = (torch.searchsorted(byp, v[None, :].expand(GW, H).contiguous(), right=True) - 1).clamp_(0, GH - 1)
+    gy = gyc[gx0][:, :].T                                               # (H, W): gyc[gx0[u], v]
+    bxp = bx[None, :] + torch.from_numpy(sx).to(device)                # (GH, GW+1) per row cell
+    gxr = (torch.searchsorted(bxp, u[None, :].expand(GH, W).contiguous(), right=True) - 1).clamp_(0, GW - 1)
+    gx = torch.gather(gxr, 0, gy)                                       # gxr[gy[v,u], u]
+    return (gy * GW + gx).to(torch.int32).contiguous(), GW, GH
+
+
+@dataclass
+class MixItem:
+    """One light field of the batched workload (views RGBA8 and labels on the device)."""
+    rig: Rig
+    views: torch.Tensor
+    labels: torch.Tensor
+    GW: int
+    GH: int
+    params: dict
+    pitch: int
+    kind: str
+
+    def item(self) -> dict:
+        return dict(views=self.views, labels=self.labels, K=self.rig.K, R=self.rig.R, t=self.rig.t, GW=self.GW,
+                    GH=self.GH, params=self.params)
+
+
+def _mix_shape(rng, scale):
+    V = int(rng.integers(4, 17))
+    W0, H0 = MIX_RESOLUTIONS[int(rng.integers(len(MIX_RESOLUTIONS)))]
+    kind = "arc" if rng.uniform() < 0.5 else "grid"
+    pitch = int(rng.integers(8, 33))
+    L = int(rng.integers(128, 257))
+    return V, _rnd(W0 * scale), _rnd(H0 * scale), kind, pitch, L
+
+
+def mix_shapes(n: int = 64, scale: float = 1.0, seed: int = SCENE_SEED_BASE + 4) -> list:
+    """(views, W, H, rig kind, pitch, labels) of each light field of make_mix, without rendering."""
+    return [_mix_shape(np.random.default_rng(seed * 1000 + i), scale) for i in range(n)]
+
+
+def make_mix(n: int = 64, device="cpu", scale: float = 1.0, seed: int = SCENE_SEED_BASE + 4, first: int = 0) -> list:
+    """The batched workload: n independent light fields, camera counts uniform in
+    4..16, resolutions from MIX_RESOLUTIONS, arc or grid rigs, perturbed grid
+    superpixels of pitch 8..32 px, 128..256 labels, 6 iterations; each with its
+    own seeded scene of the config-2 kind and its own jitter key.  `first`
+    skips the leading light fields (a sample of the same workload)."""
+    out = []
+    for i in range(first, n):
+        rng = np.random.default_rng(seed * 1000 + i)
+        V, W, H, kind, pitch, L = _mix_shape(rng, scale)
+        f = 300.0 * W / 320.0
+        if kind == "arc":
+            rig = arc_rig(V, 30.0, 5.0, f, W, H)
+        else:
+            rows = max(1, int(math.floor(math.sqrt(V))))
+            cols = -(-V // rows)
+            g = grid_rig(rows, cols, 0.08, f, W, H)
+            rig = Rig(g.K[:V].copy(), g.R[:V].copy(), g.t[:V].copy(), W, H)
+        scene = _random_scene(rng, 12, 3, 4, f, 2.0, 8.0, 1.6)
+        rgb, _, _ = render(rig, scene, device)
+        views = quantize_rgba8(rgb)
+        del rgb
+        labs, GW, GH = [], None, None
+        for v in range(V):
+            lab, GW, GH = grid_labels_fast(W, H, pitch * scale if scale < 1 else pitch, True,
+                                           seed=seed * 1000 + 100 * i + v, device=device)
+            labs.append(lab)
+        params = dict(d_min=2.0, d_max=8.0, num_labels=L, iterations=6, T=0.04, sigma=0.0, alpha=0.1, eta=0.5,
+                      kernel_size_init=0, kernel_step_sp=5.0, max_neighbor_views=8, depth_domain=0, jitter=1,
+                      term_mask=7, sweep_frame=0, seed=(seed * 1000 + i) ^ 0x5EED, lf_index=i, xy_eps=0.0,
+                      warm_iter_offset=0)
+        out.append(MixItem(rig, views, torch.stack(labs), GW, GH, params, pitch, kind))
+    return out
