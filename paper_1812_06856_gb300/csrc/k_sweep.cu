@@ -16,8 +16,11 @@
 //
 // Homography per (label, view): for the plane g = z_k * gh (gh = (0,0,1) for
 // camera-frame sweeps) A = P + q g^T; its superpixel-anchored third column
-// (P + q g^T) (ref,1) is composed in FP64 and rounded to FP32; per sample the
-// projection is 6 FP32 FMAs on offsets from the anchor.
+// (P + q g^T) (ref,1) is composed in FP64 and rounded to FP32.  In the camera
+// frame the rest, P (du, dv, 0) on the pixel's offset from the anchor, does not
+// depend on the label: it is computed once per pixel and view of a chunk into
+// shared memory and each sample adds the label's column (3 FP32 adds).  In the
+// world frame the label also scales the pixel terms: 6 FP32 FMAs per sample.
 #include "lfd_sample.cuh"
 
 namespace lfd {
@@ -33,10 +36,13 @@ struct SweepPair {
     const void *tex;
 };
 
-template <int THREADS>
+template <int THREADS, bool WORLD>
 struct SweepShared {
     float2 d[SWEEP_CHUNK];
     float4 ref[SWEEP_CHUNK];
+    // camera-frame sweeps: the label-independent part of each pixel's projection into
+    // each neighbour view, P (du, dv, 0) (the label adds q z_k at the anchor)
+    float4 xyw[WORLD ? 1 : LFD_MAXN][SWEEP_CHUNK];
     SweepPair pair[LFD_MAXN];
     double gh[4];                         // gh and gh.(ref,1)
     float n[3];                           // sweep plane normal (camera frame)
@@ -47,7 +53,7 @@ struct SweepShared {
 
 // the whole sweep of superpixel gs by one CTA (threads = labels)
 template <int FMT, bool WORLD, int THREADS>
-__device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, int gs, SweepShared<THREADS> &sh,
+__device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, int gs, SweepShared<THREADS, WORLD> &sh,
                                          float4 *planes, int *label_out, float *cost_out)
 {
     const int v = __ldg(w.sp_view + gs);
@@ -128,6 +134,16 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
                 if (WORLD) front = (sh.gh[0] * x + sh.gh[1] * y + sh.gh[2]) > 0.0 ? 1.f : 0.f;
                 sh.ref[i] = make_float4(rc.x, rc.y, rc.z, front);
             }
+            if (!WORLD) {
+                __syncthreads();
+                for (int t = threadIdx.x; t < cn * nnb; t += THREADS) {
+                    const int j = t / cn, i = t - j * cn;
+                    const SweepPair &sp = sh.pair[j];
+                    const float2 d = sh.d[i];
+                    sh.xyw[j][i] = make_float4(fmaf(sp.a00, d.x, sp.a01 * d.y), fmaf(sp.a10, d.x, sp.a11 * d.y),
+                                               fmaf(sp.a20, d.x, sp.a21 * d.y), 0.f);
+                }
+            }
             __syncthreads();
             for (int j = 0; j < nnb; j++) {
                 const SweepPair &sp = sh.pair[j];
@@ -144,16 +160,27 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
                 }
                 const void *tex = sp.tex;
                 const int Wi = sp.Wi, Hi = sp.Hi;
+                if (WORLD) {
 #pragma unroll 4
-                for (int i = 0; i < cn; i++) {
-                    const float2 d = sh.d[i];
-                    const float4 rc = sh.ref[i];
-                    const float X = fmaf(a00, d.x, fmaf(a01, d.y, cx));
-                    const float Y = fmaf(a10, d.x, fmaf(a11, d.y, cy));
-                    const float Wz = fmaf(a20, d.x, fmaf(a21, d.y, cw));
-                    float t = tssd_sample<FMT>(tex, Wi, Hi, X, Y, Wz, make_float3(rc.x, rc.y, rc.z), T);
-                    if (WORLD && rc.w == 0.f) t = T;
-                    cost += t;
+                    for (int i = 0; i < cn; i++) {
+                        const float2 d = sh.d[i];
+                        const float4 rc = sh.ref[i];
+                        const float X = fmaf(a00, d.x, fmaf(a01, d.y, cx));
+                        const float Y = fmaf(a10, d.x, fmaf(a11, d.y, cy));
+                        const float Wz = fmaf(a20, d.x, fmaf(a21, d.y, cw));
+                        float t = tssd_sample<FMT>(tex, Wi, Hi, X, Y, Wz, make_float3(rc.x, rc.y, rc.z), T);
+                        if (rc.w == 0.f) t = T;
+                        cost += t;
+                    }
+                } else {
+                    const float4 *xyw = sh.xyw[WORLD ? 0 : j];
+#pragma unroll 4
+                    for (int i = 0; i < cn; i++) {
+                        const float4 q = xyw[i];
+                        const float4 rc = sh.ref[i];
+                        cost += tssd_sample<FMT>(tex, Wi, Hi, q.x + cx, q.y + cy, q.z + cw,
+                                                 make_float3(rc.x, rc.y, rc.z), T);
+                    }
                 }
             }
         }
@@ -203,7 +230,7 @@ template <int FMT, bool WORLD, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_sweep(Workspace w, Consts c, float4 *planes, int *label_out,
                                                    float *cost_out)
 {
-    __shared__ SweepShared<THREADS> sh;
+    __shared__ SweepShared<THREADS, WORLD> sh;
     sweep_sp<FMT, WORLD, THREADS>(w, c, blockIdx.x, sh, planes, label_out, cost_out);
 }
 
@@ -212,7 +239,7 @@ template <int FMT, bool WORLD, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_sweep_persistent(Workspace w, Consts c, float4 *planes, int *label_out,
                                                               float *cost_out)
 {
-    __shared__ SweepShared<THREADS> sh;
+    __shared__ SweepShared<THREADS, WORLD> sh;
     for (;;) {
         if (threadIdx.x == 0) sh.item = atomicAdd(&w.queue[0], 1);
         __syncthreads();
