@@ -246,7 +246,7 @@ typedef struct {
                                   Needs a non-default stream. */
     int32_t sweep_threads;     /* 128 or 256 (0 = 256): labels scored in parallel per superpixel */
     int32_t sweep_persistent;  /* 1: persistent sweep CTAs take superpixels from a queue ordered
-                                  by cost (pixels x neighbour views), most expensive first */
+                                  by size (pixel-slot class ceil(n/32)), largest first */
     int32_t prop_blocks;       /* 7 or 8 (0 = 8) resident propagation CTAs per SM */
     int32_t prop_persistent;   /* 1: persistent propagation warps over the same ordered queue */
     int32_t reserved[2];       /* must be 0 */

@@ -245,7 +245,7 @@ __device__ __forceinline__ float smoothness(const SpShared &sh, float sum_w, dou
 }
 
 template <int DOMAIN>
-__device__ __forceinline__ HypF hyp_prep(const WarpSP &S, const SpShared &sh, double g0, double g1, double g2)
+__device__ __noinline__ HypF hyp_prep(const WarpSP &S, const SpShared &sh, double g0, double g1, double g2)
 {
     HypF h;
     const double gref = g0 * S.ref.x + g1 * S.ref.y + g2;
@@ -538,6 +538,36 @@ __device__ bool setup_sp(const Workspace &w, const float4 *planes_in, int gs, in
     return true;
 }
 
+// Refinement candidate t = lane (Fig. 3b): the normal of the triangle of the
+// own centroid at depth dnew and ring neighbours t, t+1 at their depths,
+// facing the camera; false for a missing vertex, a degenerate or a grazing
+// triangle.  The plane goes to the warp's CandShared slot t.
+template <int DOMAIN>
+__device__ __noinline__ bool triangle_candidate(const ViewDev &vd, double dnew, int t)
+{
+    const SpShared &sh = g_sh[threadIdx.x >> 5];
+    CandShared &cs = g_cs[threadIdx.x >> 5];
+    const SpNb &A = sh.nb[t];
+    const SpNb &B = sh.nb[(t + 1) & 7];
+    if (!A.ok || !B.ok) return false;
+    const double P0x = dnew * sh.rx, P0y = dnew * sh.ry, P0z = dnew * sh.rz;
+    const double e1x = A.Px - P0x, e1y = A.Py - P0y, e1z = A.Pz - P0z;
+    const double e2x = B.Px - P0x, e2y = B.Py - P0y, e2z = B.Pz - P0z;
+    double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    const double nn2 = nx * nx + ny * ny + nz * nz;
+    const double l12 = (e1x * e1x + e1y * e1y + e1z * e1z) * (e2x * e2x + e2y * e2y + e2z * e2z);
+    if (!(nn2 > 0.0 && nn2 >= 1e-24 * l12)) return false;               // |n| >= 1e-12 |e1| |e2|
+    const double inn = 1.0 / sqrt(nn2);
+    nx *= inn; ny *= inn; nz *= inn;
+    if (nx * P0x + ny * P0y + nz * P0z > 0.0) { nx = -nx; ny = -ny; nz = -nz; }   // face the camera
+    cs.nx[t] = (float)nx; cs.ny[t] = (float)ny; cs.nz[t] = (float)nz;
+    if (!(fabs(nx * sh.rx + ny * sh.ry + nz * sh.rz) >= 0.1 * sh.rn)) return false;   // not grazing
+    double tg0 = 0, tg1 = 0, tg2 = 0;
+    if (!plane_to_g(vd, dnew, nx, ny, nz, sh.cx, sh.cy, tg0, tg1, tg2)) return false;
+    cand_store(cs, t, hyp_prep<DOMAIN>(sh.S, sh, tg0, tg1, tg2));
+    return true;
+}
+
 // slots per lane for a superpixel of n pixels (the instantiated counts)
 __device__ __forceinline__ int slot_class(int n)
 {
@@ -558,7 +588,7 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     SpShared &sh = g_sh[wid];
     CandShared &cs = g_cs[wid];
-    const WarpSP S = sh.S;
+    const WarpSP &S = sh.S;                  // read from shared memory where used: nothing to spill
     const dbl4 gc = w.sp_g[gs];
     const ViewDev &vd = w.views[S.v];
     unsigned n_hyp = 0;
@@ -637,31 +667,7 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
     int best_t = -1;
     const double dnew = best_m > 0 ? 1.0 / sh.best_ig : (double)planes_in[gs].x;
     if (Ebest > -INFINITY && dnew > 0.0) {
-        const double P0x = dnew * sh.rx, P0y = dnew * sh.ry, P0z = dnew * sh.rz;
-        bool ok = false;
-        if (lane < 8) {
-            const SpNb &A = sh.nb[lane];
-            const SpNb &B = sh.nb[(lane + 1) & 7];
-            ok = A.ok && B.ok;
-            if (ok) {
-                const double e1x = A.Px - P0x, e1y = A.Py - P0y, e1z = A.Pz - P0z;
-                const double e2x = B.Px - P0x, e2y = B.Py - P0y, e2z = B.Pz - P0z;
-                double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-                const double nn2 = nx * nx + ny * ny + nz * nz;
-                const double l12 = (e1x * e1x + e1y * e1y + e1z * e1z) * (e2x * e2x + e2y * e2y + e2z * e2z);
-                ok = nn2 > 0.0 && nn2 >= 1e-24 * l12;                     // |n| >= 1e-12 |e1| |e2|
-                if (ok) {
-                    const double inn = 1.0 / sqrt(nn2);
-                    nx *= inn; ny *= inn; nz *= inn;
-                    if (nx * P0x + ny * P0y + nz * P0z > 0.0) { nx = -nx; ny = -ny; nz = -nz; }   // face the camera
-                    ok = fabs(nx * sh.rx + ny * sh.ry + nz * sh.rz) >= 0.1 * sh.rn;              // not grazing
-                    double tg0 = 0, tg1 = 0, tg2 = 0;
-                    if (ok) ok = plane_to_g(vd, dnew, nx, ny, nz, sh.cx, sh.cy, tg0, tg1, tg2);
-                    if (ok) cand_store(cs, lane, hyp_prep<DOMAIN>(S, sh, tg0, tg1, tg2));
-                    cs.nx[lane] = (float)nx; cs.ny[lane] = (float)ny; cs.nz[lane] = (float)nz;
-                }
-            }
-        }
+        const bool ok = lane < 8 && triangle_candidate<DOMAIN>(vd, dnew, lane);
         cs.ec[lane] = 0.f;
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         __syncwarp();
@@ -737,7 +743,7 @@ __device__ __forceinline__ void propagate_one(const Workspace &w, const Consts &
 }
 
 template <int DOMAIN, int MINB>
-__global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate(Workspace w, Consts c, int iter,
+__global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate(const __grid_constant__ Workspace w, Consts c, int iter,
                                                                      const float4 *planes_in, float4 *planes_out,
                                                                      int *choice, float *energy)
 {
@@ -749,7 +755,7 @@ __global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate(Workspace w
 
 // persistent warps: superpixels taken from the cost-ordered queue, most expensive first
 template <int DOMAIN, int MINB>
-__global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate_persistent(Workspace w, Consts c, int iter,
+__global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate_persistent(const __grid_constant__ Workspace w, Consts c, int iter,
                                                                                 const float4 *planes_in,
                                                                                 float4 *planes_out, int *choice,
                                                                                 float *energy)
@@ -804,7 +810,7 @@ cudaError_t launch_propagate(const Workspace &w, const Consts &c, const LaunchCf
 // ---------------------------------------------------------------------------
 
 template <int FMT, int DOMAIN>
-__global__ void __launch_bounds__(128) k_score(Workspace w, Consts c, const float4 *planes_state, int nq,
+__global__ void __launch_bounds__(128) k_score(const __grid_constant__ Workspace w, Consts c, const float4 *planes_state, int nq,
                                                const lfd_query *q, float *out)
 {
     const int qi = blockIdx.x * 4 + (threadIdx.x >> 5);

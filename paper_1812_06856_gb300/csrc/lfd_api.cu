@@ -408,7 +408,7 @@ cudaError_t traced(lfd_ctx *ctx, int stage, cudaStream_t st, F launch)
 }
 
 // -- layout + workspace allocation -------------------------------------------
-constexpr int ORDER_BUCKETS_HOST = 1024;
+constexpr int ORDER_KEYS_HOST = 17;   // size classes of the work order
 
 // Sizes of the bound views in call order (global numbering).
 lfd_status make_layout(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, Layout &L)
@@ -450,7 +450,7 @@ size_t workspace_need(const Layout &L, int fmt)
     add(4 * S); add(4 * (S + 1)); add(4 * S); add(4 * P);
     add(8 * S); add(16 * S); add(16 * S); add(32 * S); add(16 * S); add(16 * S);
     add(sizeof(DevCounters));
-    add(4 * S); add(4 * ORDER_BUCKETS_HOST); add(16); add(sizeof(float *) * V);
+    add(4 * S); add(4 * ORDER_KEYS_HOST); add(16); add(sizeof(float *) * V);
     add(16 * S); add(16 * S); add(4 * S); add(8 * S); add(8 * S);
     for (int v = 0; v < V; v++) add((size_t)qb * L.W[v] * L.H[v]);
     for (int v = 0; v < V; v++) add((size_t)16 * L.W[v] * L.H[v]);
@@ -509,7 +509,7 @@ lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
     ctx->d_bbox = (int4 *)a.take(16 * S);
     ctx->d_ctr = (DevCounters *)a.take(sizeof(DevCounters));
     ctx->d_order = (int *)a.take(4 * S);
-    ctx->d_hist = (int *)a.take(4 * ORDER_BUCKETS_HOST);
+    ctx->d_hist = (int *)a.take(4 * ORDER_KEYS_HOST);
     ctx->d_queue = (int *)a.take(16);
     ctx->d_depth_ptrs = (float **)a.take(sizeof(float *) * V);
     ctx->d_planesA = (float4 *)a.take(16 * S);
@@ -700,7 +700,7 @@ lfd_status enqueue_input(lfd_ctx *ctx, cudaStream_t st, bool record_event)
     }));
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_sp_minw(ctx->w, ctx->c, ctx->d_sp_col, st); }));
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_quads(ctx->w, V, L.max_px, ctx->fmt, st); }));
-    // superpixels by descending cost: the propagation kernels take them in this order
+    // work order of the propagation kernels: by descending size class, index order inside
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st,
                     [&] { return launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, st); }));
     return LFD_OK;

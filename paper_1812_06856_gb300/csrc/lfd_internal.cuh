@@ -104,7 +104,7 @@ struct Workspace {
     const short *radii;      // [V][LFD_MAX_ITER_INDEX + 1][LFD_MAX_RADII]
     const int *radii_cnt;    // [V][LFD_MAX_ITER_INDEX + 1]
     DevCounters *ctr;
-    const int *order;        // [S_total] superpixels by descending cost (persistent launches)
+    const int *order;        // [S_total] work order: descending pixel-slot class, index order inside
     int *queue;              // [4] work-queue counters of persistent launches
     int S_total;
     long long px_total;
@@ -190,7 +190,7 @@ cudaError_t launch_sp_collect(const Workspace &w, const Consts &c, const int4 *b
                               double2 *cen, int2 *ref, float4 *col, cudaStream_t st);
 cudaError_t launch_sp_minw(const Workspace &w, const Consts &c, float4 *col, cudaStream_t st);
 cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStream_t st);
-cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, cudaStream_t st);
+cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, cudaStream_t st);  // hist: 17 ints
 cudaError_t launch_sweep(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
                          float *cost, cudaStream_t st);
 cudaError_t launch_plane_prep(const Workspace &w, const Consts &c, const float4 *planes, double4_32a *g, float4 *rc,
