@@ -232,7 +232,7 @@ lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const 
 /* ---- batched frames --------------------------------------------------- */
 
 /* Launch options of lfd_estimate_batch (lfd_batch_options_default fills
- * autotune 0, graph 0, sweep_threads 256, sweep_persistent 0, prop_blocks 8,
+ * autotune 0, graph 0, sweep_threads 256, sweep_persistent 1, prop_blocks 8,
  * prop_persistent 1). */
 typedef struct {
     int32_t autotune;          /* 1: the first call with a new argument signature times the

@@ -182,7 +182,7 @@ struct lfd_ctx {
     std::vector<LfInfo> lfs;
     std::vector<int> nbr;          // [V_total * 8] global view indices
     int fmt = 0;
-    LaunchCfg lc{256, 0, 8, 1, 0};
+    LaunchCfg lc{256, 1, 8, 1, 0};
     // workspace
     Arena ws;
     Workspace w{};
@@ -1035,6 +1035,7 @@ void lfd_batch_options_default(lfd_batch_options *o)
     if (!o) return;
     memset(o, 0, sizeof(*o));
     o->sweep_threads = 256;
+    o->sweep_persistent = 1;
     o->prop_blocks = 8;
     o->prop_persistent = 1;
 }

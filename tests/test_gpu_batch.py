@@ -75,7 +75,7 @@ def test_batch_equals_separate_calls(lfd, two_rigs):
 
 @pytest.mark.parametrize("opt", [
     dict(sweep_threads=128),
-    dict(sweep_persistent=1),
+    dict(sweep_persistent=0),
     dict(prop_blocks=7),
     dict(prop_persistent=0),
     dict(sweep_threads=128, sweep_persistent=1, prop_blocks=7, prop_persistent=1),
