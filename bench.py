@@ -58,18 +58,51 @@ def kernel_source_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload_key: str):
-    """DRAM bytes per launch of `kernel` from the ncu capture recorded in
-    profiles/dram_traffic.txt, or None when the kernel's sources changed since."""
+def recorded_traffic(kernel: str, workload_key: str, column: int = 2):
+    """DRAM bytes (column 2) or L2 bytes (column 4) per launch of `kernel` from
+    the ncu capture recorded in profiles/dram_traffic.txt, or None when the
+    kernel's sources changed since."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         for line in f:
             parts = line.split()
-            if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload_key:
-                return float(parts[2]) if parts[3] == kernel_source_hash(kernel) else None
+            if len(parts) > max(column, 3) and not line.startswith("#") and parts[0] == kernel and parts[1] == workload_key:
+                return float(parts[column]) if parts[3] == kernel_source_hash(kernel) else None
     return None
+
+
+def l2_copy_peak_gbs(dev) -> float:
+    """L2 bandwidth of a plain copy whose 32 MiB working set stays in L2
+    (read + write bytes, best of 20 CUDA-event timed copies)."""
+    a = torch.empty(4 << 20, dtype=torch.float32, device=dev).fill_(1.0)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    best = float("inf")
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 10)
+    return 2 * a.numel() * 4 / (best / 1000.0) / 1e9
+
+
+def level_rates(kernel: str, wkey: str, avg_launch_ms: float, dev) -> dict:
+    """Memory-level view of the dominant kernel beside its FP32 roofline:
+    DRAM and L2 bytes per launch from the recorded ncu capture over the live
+    launch time, against the measured HBM copy peak and an L2 copy peak
+    measured here."""
+    dram = recorded_traffic(kernel, wkey, 2)
+    l2 = recorded_traffic(kernel, wkey, 4)
+    sec = avg_launch_ms / 1000.0
+    return {"hbm_peak_gbs": measured_peaks().get("hbm_gbs"), "l2_copy_peak_gbs": l2_copy_peak_gbs(dev),
+            "dram_gbs": dram / sec / 1e9 if dram else None, "l2_gbs": l2 / sec / 1e9 if l2 else None,
+            "note": "bytes per launch from profiles/dram_traffic.txt (ncu), time from this run's CUDA events"}
 
 
 def workload_name(cfg: int, lf) -> str:
@@ -323,7 +356,7 @@ def run_ours(args):
                              f"{sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
                 "algorithmic": f"{FLOPS_PER_SAMPLE[dom]} FP32 flop per pixel-view sample x "
                                f"{dom_samples / launches:.4g} samples per launch",
-                "avg_launch_ms": avg_launch_ms}
+                "avg_launch_ms": avg_launch_ms, "levels": level_rates(f"k_{dom}", wkey, avg_launch_ms, dev)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -15,6 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lfd_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "lfd_fusion_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
@@ -25,9 +26,10 @@ MAXN = 8
 def build(force: bool = False) -> str:
     """Compile the oracle with the host C compiler (portable flags only)."""
     with _lock:
-        if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        stale = not os.path.exists(_LIB_PATH) or any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(f) for f in _SRCS)
+        if force or stale:
             tmp = _LIB_PATH + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, *_SRCS, "-lm"])
             os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -115,6 +117,7 @@ def _load():
         lib.orc_refine_candidates.restype = i32
         lib.orc_refine_candidates.argtypes = [vp, vp, i32, f64, vp]
         lib.orc_score.argtypes = [vp, vp, vp, i32, vp]
+        lib.orc_fuse.argtypes = [i32, vp, vp, vp, vp, vp, vp, f64, vp, vp]
         lib.orc_terms_size.restype = i32
         lib.orc_query_size.restype = i32
         lib.orc_input_size.restype = i32
@@ -150,6 +153,26 @@ def bilinear_image(rgb: np.ndarray, x: float, y: float) -> np.ndarray:
     out = np.zeros(3)
     _load().orc_bilinear_image(_p(rgb), rgb.shape[1], rgb.shape[0], x, y, _p(out))
     return out
+
+
+def fuse(K, R, t, depths, tau: float = 0.01):
+    """Stability-based depth fusion (Section III-D), lfd_fusion_oracle.c.
+    K, R, t: (V,3,3), (V,3,3), (V,3); depths: list of (H_v, W_v) arrays.
+    Returns (fused depths, flags) as lists of arrays."""
+    lib = _load()
+    V = len(depths)
+    K = np.ascontiguousarray(K, dtype=np.float64).reshape(V, 9)
+    R = np.ascontiguousarray(R, dtype=np.float64).reshape(V, 9)
+    t = np.ascontiguousarray(t, dtype=np.float64).reshape(V, 3)
+    ds = [np.ascontiguousarray(d, dtype=np.float64) for d in depths]
+    W = np.array([d.shape[1] for d in ds], dtype=np.int32)
+    H = np.array([d.shape[0] for d in ds], dtype=np.int32)
+    outs = [np.zeros_like(d) for d in ds]
+    flags = [np.zeros(d.shape, dtype=np.uint8) for d in ds]
+    arr = lambda xs: (C.c_void_p * V)(*[x.ctypes.data for x in xs])
+    pin, pout, pfl = arr(ds), arr(outs), arr(flags)
+    lib.orc_fuse(V, _p(K), _p(R), _p(t), _p(W), _p(H), pin, float(tau), pout, pfl)
+    return outs, flags
 
 
 def terms_to_dict(t: Terms, n: int) -> dict:
