@@ -229,6 +229,23 @@ lfd_status lfd_estimate(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_params
 lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const lfd_params *p,
                              float *const *planes_out_host, float *const *depth_out_host, void *stream);
 
+/* ---- depth fusion (step after the hot path) ---------------------------- */
+
+/* Stability-based depth fusion (Section III-D) of one depth map per bound
+ * view, light field by light field.  Each view in turn is the reference:
+ * every pixel of every other view of its light field with a depth > 0 is
+ * lifted to a 3-D point and projected to the reference's nearest pixel
+ * (floor(x + 0.5), valid iff in front and 0 <= x <= W-1, 0 <= y <= H-1);
+ * per other view the point of smallest depth wins a pixel.  Each depth
+ * candidate of a reference pixel (its own depth when > 0 and one per other
+ * view) gets stability = #candidates with |z - z_c| <= tau z_c minus #others;
+ * the closest candidate with stability >= 0 is written (0 if none).
+ *   depth_in / depth_out: host arrays [V] of device float[H*W] (the layout of
+ *   lfd_estimate's depth maps); must not alias.  tau > 0 (0.01 = 1 %).
+ * The z-buffers (V_l - 1 planes per view of the largest light field) are
+ * allocated on first use outside the context's budget.  Asynchronous. */
+lfd_status lfd_fuse(lfd_ctx *ctx, const float *const *depth_in, float *const *depth_out, double tau, void *stream);
+
 /* ---- batched frames --------------------------------------------------- */
 
 /* Launch options of lfd_estimate_batch (lfd_batch_options_default fills
@@ -363,7 +380,8 @@ enum {
     LFD_STAGE_SWEEP = 1,        /* steps a2-a4 */
     LFD_STAGE_RASTER = 2,       /* step a5 (plane coefficients + rasteriser) */
     LFD_STAGE_PROPAGATE = 3,    /* steps a6-a7 */
-    LFD_STAGES = 4
+    LFD_STAGE_FUSION = 4,       /* lfd_fuse (Section III-D) */
+    LFD_STAGES = 5
 };
 
 /* Enable (1) or disable (0) CUDA-event timing of every kernel launch of the

@@ -97,11 +97,16 @@ void orc_fuse(int32_t V, const double *K, const double *R, const double *t, cons
                                      fabs(vv - (Hr - 1)) < MARGIN_PX;
                     const int rounding = frac_dist_half(u) < MARGIN_PX || frac_dist_half(vv) < MARGIN_PX;
                     const int qx = (int)floor(u + 0.5), qy = (int)floor(vv + 0.5);
-                    if (edge || rounding) {         /* the point may land on a neighbouring pixel too */
-                        for (int dy = -1; dy <= 1; dy++)
-                            for (int dx = -1; dx <= 1; dx++) {
-                                const int ax = qx + dx, ay = qy + dy;
-                                if (ax >= 0 && ay >= 0 && ax < Wr && ay < Hr) fl[(size_t)ay * Wr + ax] = 1;
+                    if (edge || rounding) {
+                        /* the point may land on q or, across an ambiguous rounding boundary,
+                           on the neighbour on the other side of it; flag those pixels */
+                        const int ax = frac_dist_half(u) < MARGIN_PX ? (u + 0.5 - qx < 0.5 ? qx - 1 : qx + 1) : qx;
+                        const int ay = frac_dist_half(vv) < MARGIN_PX ? (vv + 0.5 - qy < 0.5 ? qy - 1 : qy + 1) : qy;
+                        const int xs[2] = {qx, ax}, ys[2] = {qy, ay};
+                        for (int b = 0; b < 2; b++)
+                            for (int c = 0; c < 2; c++) {
+                                const int px = xs[b], py = ys[c];
+                                if (px >= 0 && py >= 0 && px < Wr && py < Hr) fl[(size_t)py * Wr + px] = 1;
                             }
                     }
                     if (!in) continue;

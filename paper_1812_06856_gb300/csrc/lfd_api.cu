@@ -220,14 +220,20 @@ struct lfd_ctx {
     bool prof = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_used;
     std::vector<cudaEvent_t> prof_free;
-    long long launches[LFD_STAGES] = {0, 0, 0, 0};
+    long long launches[LFD_STAGES] = {};
     // pinned upload staging (records) and depth-pointer table
     PinnedRing stage;                // view/pair/radii records
     PinnedRing dtab;                 // depth-output pointer tables
+    PinnedRing ftab;                 // fusion tables
+    std::vector<lfd_camera> cams;    // cameras of the bound views (global order)
+    unsigned *d_zbuf = nullptr;      // fusion z-buffers (one light field at a time)
+    size_t zbuf_cap = 0;
+    void *d_ftab = nullptr;
+    size_t ftab_cap = 0;
     // CUDA graph of a batched frame and the pinned depth table it reads
     cudaGraphExec_t gexec = nullptr;
     uint64_t gsig = 0;
-    long long glaunches[LFD_STAGES] = {0, 0, 0, 0};
+    long long glaunches[LFD_STAGES] = {};
     float **h_bdepth = nullptr;
     int h_bdepth_cap = 0;
     cudaEvent_t ev_bdepth = nullptr;
@@ -569,6 +575,8 @@ lfd_status plan_input(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, const lfd_
     const int V = L.V;
     ctx->fmt = lfs[0].fmt;
     ctx->lfs.clear();
+    ctx->cams.clear();
+    for (int l = 0; l < n; l++) ctx->cams.insert(ctx->cams.end(), lfs[l].cams, lfs[l].cams + lfs[l].num_views);
     ctx->nbr.assign((size_t)V * LFD_MAXN, -1);
     Consts c{};
     c.V = V;
@@ -1055,11 +1063,12 @@ lfd_status lfd_create(lfd_ctx **out, int32_t device, uint64_t hbm_budget_bytes)
     ctx->budget = hbm_budget_bytes;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        ctx->stage.init() != cudaSuccess || ctx->dtab.init() != cudaSuccess ||
+        ctx->stage.init() != cudaSuccess || ctx->dtab.init() != cudaSuccess || ctx->ftab.init() != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_bdepth, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         ctx->stage.release();
         ctx->dtab.release();
+        ctx->ftab.release();
         if (ctx->ev_bdepth) cudaEventDestroy(ctx->ev_bdepth);
         delete ctx;
         return LFD_ERR_CUDA;
@@ -1083,6 +1092,9 @@ lfd_status lfd_destroy(lfd_ctx *ctx)
     if (ctx->d_qout) cudaFree(ctx->d_qout);
     ctx->stage.release();
     ctx->dtab.release();
+    ctx->ftab.release();
+    if (ctx->d_zbuf) cudaFree(ctx->d_zbuf);
+    if (ctx->d_ftab) cudaFree(ctx->d_ftab);
     if (ctx->h_bdepth) cudaFreeHost(ctx->h_bdepth);
     if (ctx->ev_bdepth) cudaEventDestroy(ctx->ev_bdepth);
     for (auto &u : ctx->prof_used) {
@@ -1384,6 +1396,98 @@ lfd_status lfd_workspace_required(int32_t n, const lfd_lightfield *lfs, uint64_t
     return LFD_OK;
 }
 
+
+lfd_status lfd_fuse(lfd_ctx *ctx, const float *const *depth_in, float *const *depth_out, double tau, void *stream)
+{
+    lfd_status s;
+    if ((s = need_bound(ctx)) != LFD_OK) return s;
+    if ((s = set_device(ctx)) != LFD_OK) return s;
+    if (!depth_in || !depth_out) return fail(ctx, LFD_ERR_INVALID_ARG, "depth_in / depth_out is NULL");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(ctx, LFD_ERR_INVALID_ARG, "tau must be > 0");
+    for (int v = 0; v < ctx->L.V; v++) {
+        if (!depth_in[v] || !depth_out[v]) return fail(ctx, LFD_ERR_INVALID_ARG, "depth map of view %d is NULL", v);
+        if (depth_in[v] == depth_out[v]) return fail(ctx, LFD_ERR_INVALID_ARG, "view %d: depth_in aliases depth_out", v);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // z-buffer and table sizes: the largest light field
+    size_t zmax = 0, tmax = 0;
+    for (const LfInfo &l : ctx->lfs) {
+        size_t z = 0;
+        for (int k = 0; k < l.V; k++) z += (size_t)(l.V - 1) * ctx->L.W[l.first_view + k] * ctx->L.H[l.first_view + k];
+        zmax = std::max(zmax, z);
+        const size_t t = align_up(8 * (size_t)l.V, 16) + 8 * (size_t)l.V + 16 * (size_t)l.V + 48 * (size_t)l.V * l.V;
+        tmax = std::max(tmax, t);
+    }
+    if ((s = ensure_dev(ctx, (void **)&ctx->d_zbuf, &ctx->zbuf_cap, 4 * std::max<size_t>(zmax, 1))) != LFD_OK) return s;
+    if ((s = ensure_dev(ctx, &ctx->d_ftab, &ctx->ftab_cap, tmax)) != LFD_OK) return s;
+    for (const LfInfo &l : ctx->lfs) {
+        const int V = l.V, f = l.first_view;
+        // table: W, H (int), zoff (int64), depth_in, depth_out (pointers), mats (float)
+        const size_t o_wh = 0, o_zoff = align_up(8 * (size_t)V, 16), o_in = o_zoff + 8 * (size_t)V,
+                     o_out = o_in + 8 * (size_t)V, o_mats = o_out + 8 * (size_t)V;
+        const size_t bytes = o_mats + 48 * (size_t)V * V;
+        LFD_CUDA(ctx->ftab.next(bytes));
+        char *h = (char *)ctx->ftab.buf();
+        int *hw = (int *)(h + o_wh), *hh = hw + V;
+        long long *hz = (long long *)(h + o_zoff);
+        const float **hin = (const float **)(h + o_in);
+        float **hout = (float **)(h + o_out);
+        float *hm = (float *)(h + o_mats);
+        long long zw = 0;
+        int max_px = 0;
+        for (int k = 0; k < V; k++) {
+            hw[k] = ctx->L.W[f + k];
+            hh[k] = ctx->L.H[f + k];
+            hz[k] = zw;
+            zw += (long long)(V - 1) * hw[k] * hh[k];
+            max_px = std::max(max_px, hw[k] * hh[k]);
+            hin[k] = depth_in[f + k];
+            hout[k] = depth_out[f + k];
+        }
+        for (int i = 0; i < V; i++) {
+            const lfd_camera &ci = ctx->cams[f + i];
+            double Ki[9];
+            inv_pinhole(ci.K, Ki);
+            for (int r = 0; r < V; r++) {
+                float *m = hm + 12 * (i * V + r);
+                if (r == i) {
+                    for (int k = 0; k < 12; k++) m[k] = 0.f;
+                    continue;
+                }
+                const lfd_camera &cr = ctx->cams[f + r];
+                // A = R_r R_i^T, M = K_r A K_i^-1, e = K_r (t_r - A t_i)
+                double A[9], KA[9], M[9], e0[3];
+                for (int a = 0; a < 3; a++)
+                    for (int b = 0; b < 3; b++)
+                        A[3 * a + b] = cr.R[3 * a] * ci.R[3 * b] + cr.R[3 * a + 1] * ci.R[3 * b + 1] +
+                                       cr.R[3 * a + 2] * ci.R[3 * b + 2];
+                mat_mul(cr.K, A, KA);
+                mat_mul(KA, Ki, M);
+                for (int a = 0; a < 3; a++)
+                    e0[a] = cr.t[a] - (A[3 * a] * ci.t[0] + A[3 * a + 1] * ci.t[1] + A[3 * a + 2] * ci.t[2]);
+                for (int k = 0; k < 9; k++) m[k] = (float)M[k];
+                for (int a = 0; a < 3; a++)
+                    m[9 + a] = (float)(cr.K[3 * a] * e0[0] + cr.K[3 * a + 1] * e0[1] + cr.K[3 * a + 2] * e0[2]);
+            }
+        }
+        LFD_CUDA(cudaMemcpyAsync(ctx->d_ftab, h, bytes, cudaMemcpyHostToDevice, st));
+        LFD_CUDA(cudaEventRecord(ctx->ftab.event(), st));
+        char *d = (char *)ctx->d_ftab;
+        FuseArgs a;
+        a.V = V;
+        a.tau = (float)tau;
+        a.W = (const int *)(d + o_wh);
+        a.H = a.W + V;
+        a.zoff = (const long long *)(d + o_zoff);
+        a.depth_in = (const float *const *)(d + o_in);
+        a.depth_out = (float *const *)(d + o_out);
+        a.mats = (const float *)(d + o_mats);
+        a.zbuf = ctx->d_zbuf;
+        LFD_CUDA(traced(ctx, LFD_STAGE_FUSION, st, [&] { return launch_fuse(a, zw, max_px, st); }));
+    }
+    return LFD_OK;
+}
+
 lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out)
 {
     if (!ctx || !out) return LFD_ERR_INVALID_ARG;
@@ -1513,7 +1617,7 @@ lfd_status lfd_profile_read(lfd_ctx *ctx, double *ms_out, int64_t *launches_out)
     if (!ctx) return LFD_ERR_INVALID_ARG;
     lfd_status s;
     if ((s = set_device(ctx)) != LFD_OK) return s;
-    double ms[LFD_STAGES] = {0, 0, 0, 0};
+    double ms[LFD_STAGES] = {};
     for (auto &u : ctx->prof_used) {
         LFD_CUDA(cudaEventSynchronize(u.second.second));
         float t = 0.f;

@@ -110,6 +110,18 @@ struct Workspace {
     long long px_total;
 };
 
+// arguments of the fusion kernels for one light field (device arrays)
+struct FuseArgs {
+    int V;                           // views of the light field
+    float tau;                       // relative agreement tolerance
+    const int *W, *H;                // [V]
+    const long long *zoff;           // [V] word offset of reference view r's z-buffer planes
+    const float *const *depth_in;    // [V]
+    float *const *depth_out;         // [V]
+    const float *mats;               // [V * V][12]: M (row-major 3x3) and e of source i -> reference r
+    unsigned *zbuf;
+};
+
 // ---------------------------------------------------------------------------
 // small device helpers
 // ---------------------------------------------------------------------------
@@ -199,6 +211,7 @@ cudaError_t launch_rasterize(const Workspace &w, const Consts &c, float *const *
 cudaError_t launch_propagate(const Workspace &w, const Consts &c, const LaunchCfg &lc, int iter,
                              const float4 *planes_in, float4 *planes_out, int *choice, float *energy,
                              cudaStream_t st);
+cudaError_t launch_fuse(const FuseArgs &a, long long zbuf_words, int max_px, cudaStream_t st);
 cudaError_t launch_score(const Workspace &w, const Consts &c, const float4 *planes_state, int nq, const lfd_query *q,
                          float *out, cudaStream_t st);
 }  // namespace lfd

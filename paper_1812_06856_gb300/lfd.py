@@ -123,6 +123,7 @@ def load(build_if_missing: bool = True):
     lib.lfd_estimate_batch.argtypes = [vp, i32, P(LightFieldC), P(Params), P(vp), P(vp), P(BatchOptions), vp]
     lib.lfd_launch_config.argtypes = [vp, P(i32)]
     lib.lfd_workspace_required.argtypes = [i32, P(LightFieldC), P(C.c_uint64)]
+    lib.lfd_fuse.argtypes = [vp, P(vp), P(vp), C.c_double, vp]
     lib.lfd_server_create.argtypes = [P(vp), i32, C.c_uint64, i32]
     lib.lfd_server_destroy.argtypes = [vp]
     lib.lfd_server_last_error.argtypes = [vp]
@@ -137,7 +138,7 @@ def load(build_if_missing: bool = True):
     for name in ("lfd_create", "lfd_destroy", "lfd_set_input", "lfd_num_superpixels", "lfd_plane_sweep",
                  "lfd_rasterize", "lfd_iterate", "lfd_estimate", "lfd_estimate_host", "lfd_synchronize",
                  "lfd_counters", "lfd_score", "lfd_get_superpixels", "lfd_neighbor_views", "lfd_profile_enable",
-                 "lfd_profile_read", "lfd_estimate_batch", "lfd_launch_config", "lfd_workspace_required",
+                 "lfd_profile_read", "lfd_estimate_batch", "lfd_launch_config", "lfd_workspace_required", "lfd_fuse",
                  "lfd_server_create", "lfd_server_destroy", "lfd_server_configure", "lfd_server_submit",
                  "lfd_server_poll", "lfd_server_export_state", "lfd_server_import_state"):
         getattr(lib, name).restype = i32
@@ -441,6 +442,25 @@ class Context:
                                                 C.byref(o), _stream(stream)), "lfd_estimate_batch")
         return planes, depths
 
+    def fuse(self, depth_in, tau: float = 0.01, stream=None):
+        """Stability-based fusion (lfd_fuse) of one depth map per bound view:
+        depth_in is a (V, H, W) float32 cuda tensor or a list of (H_v, W_v)
+        tensors; returns the fused maps in the same form."""
+        maps = [depth_in[v] for v in range(depth_in.shape[0])] if torch.is_tensor(depth_in) else list(depth_in)
+        assert len(maps) == self.V, "one depth map per bound view"
+        maps = [m.contiguous() for m in maps]
+        if torch.is_tensor(depth_in):
+            out = torch.zeros_like(depth_in)
+            outs = [out[v] for v in range(self.V)]
+        else:
+            outs = [torch.zeros_like(m) for m in maps]
+            out = outs
+        pin = _ptr_array([m.data_ptr() for m in maps])
+        pout = _ptr_array([o.data_ptr() for o in outs])
+        self._keep = [self._keep, pin, pout, maps, outs]
+        self._check(self.lib.lfd_fuse(self.h, pin, pout, float(tau), _stream(stream)), "lfd_fuse")
+        return out
+
     def launch_config(self) -> dict:
         out = (C.c_int32 * 4)()
         self._check(self.lib.lfd_launch_config(self.h, out), "lfd_launch_config")
@@ -454,14 +474,14 @@ class Context:
         self._check(self.lib.lfd_counters(self.h, C.byref(a), C.byref(b), _stream(stream)), "lfd_counters")
         return int(a.value), int(b.value)
 
-    STAGES = ("superpixels", "sweep", "raster", "propagate")
+    STAGES = ("superpixels", "sweep", "raster", "propagate", "fusion")
 
     def profile_enable(self, on: bool = True):
         self._check(self.lib.lfd_profile_enable(self.h, 1 if on else 0), "lfd_profile_enable")
 
     def profile_read(self) -> dict:
-        ms = (C.c_double * 4)()
-        n = (C.c_int64 * 4)()
+        ms = (C.c_double * len(self.STAGES))()
+        n = (C.c_int64 * len(self.STAGES))()
         self._check(self.lib.lfd_profile_read(self.h, ms, n), "lfd_profile_read")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.STAGES)}
 
