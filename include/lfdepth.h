@@ -122,6 +122,15 @@ typedef struct {
     int32_t lf_index;            /* light-field index mixed into the jitter key [0] */
     double xy_eps;               /* relative tolerance of the X/Y split of Eq. 10/11 [0] */
     int32_t warm_iter_offset;    /* iteration I of Eq. 4 is iter + offset (warm starts) [0] */
+    /* Flagged variant, not in the paper (which never refines depth continuously):
+     * after the 8 triangle normals, the refinement step also scores
+     * perturb_samples random planes around the propagated plane (d, n): depth
+     * d (1 + r (2u - 1)), normal normalize(n + r (2u' - 1, 2u'' - 1, 2u''' - 1)),
+     * r = perturb_scale 2^(1 - I), u from SplitMix64 of seed ^ 0x5045525455524231
+     * and key ((((lf*2^12 + v)*2^20 + s)*2^7 + I)*2^7 + 4k + j); the first
+     * strictly better one wins.  0..24 samples [0 = off], scale >= 0 [0.05]. */
+    int32_t perturb_samples;
+    double perturb_scale;
 } lfd_params;
 
 /* one hypothesis for lfd_score(): plane {d, n} of superpixel `sp` of `view` */

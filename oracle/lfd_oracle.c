@@ -86,6 +86,8 @@ typedef struct {
     int32_t lf_index;
     double xy_eps;                     /* relative tolerance of the X/Y split */
     int32_t warm_iter_offset;
+    int32_t perturb_samples;           /* flagged variant: random plane samples per refinement (0 = off) */
+    double perturb_scale;              /* their relative radius at I = 1, halved per iteration */
     int32_t threads;
     double margin_px, margin_rel;
 } orc_input;
@@ -944,8 +946,24 @@ static void put3(double *dst, double E, double lo, double hi) { dst[0] = E; dst[
  * normal of the triangle (own centroid point at depth dnew, centroid points of
  * two consecutive ring neighbours at their current depths).  Evaluates every
  * valid triangle; returns the first strictly better one (or -1). */
-static int refine_step(const orc_ctx *c, const orc_view *w, int s, double dnew, double Ebase,
-                       double *keep, double *Eout, int *flag, double *ref_out)
+#define ORC_REF_MAX 32   /* refinement candidates: 8 triangles + up to 24 perturbation samples */
+
+/* uniform [0,1) draw j of the perturbation variant for superpixel s of view v
+ * at iteration I: SplitMix64 of a key of its own (seed xor "PERTURB1") */
+static double perturb_u(uint64_t seed, int32_t lf, int32_t v, int32_t s, int32_t I, int32_t j)
+{
+    uint64_t key = ((((uint64_t)lf << 12) + (uint64_t)v) << 20) + (uint64_t)s;
+    key = (key << 7) + (uint64_t)I;
+    key = (key << 7) + (uint64_t)j;
+    return (double)(orc_splitmix64((seed ^ 0x5045525455524231ULL) ^ key) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* Refinement of superpixel s (Fig. 3b): the 8 ring-triangle normals at depth
+ * dnew, then -- flagged variant, not in the paper -- perturbation_samples
+ * random planes around (dnew, nbase) with a radius halving per iteration I;
+ * the first strictly better candidate in this order wins. */
+static int refine_step(const orc_ctx *c, const orc_view *w, int v, int s, double dnew, const double *nbase, int I,
+                       double Ebase, double *keep, double *Eout, int *flag, double *ref_out)
 {
     int gx = s % w->GW, gy = s / w->GW;
     double cu = w->cen[2 * s], cv = w->cen[2 * s + 1];
@@ -994,6 +1012,33 @@ static int refine_step(const orc_ctx *c, const orc_view *w, int s, double dnew, 
             keep[0] = dnew; keep[1] = n[0]; keep[2] = n[1]; keep[3] = n[2];
         }
     }
+    const int K = c->in.perturb_samples;
+    const double rad = ldexp(c->in.perturb_scale, 1 - I);
+    for (int k = 0; k < K && 8 + k < ORC_REF_MAX; k++) {
+        if (ref_out) put3(ref_out + 3 * (8 + k), -INFINITY, -INFINITY, -INFINITY);
+        double u[4];
+        for (int j = 0; j < 4; j++) u[j] = perturb_u(c->in.seed, c->in.lf_index, v, s, I, 4 * k + j);
+        const double dp = dnew * (1.0 + rad * (2.0 * u[0] - 1.0));
+        double n[3] = {nbase[0] + rad * (2.0 * u[1] - 1.0), nbase[1] + rad * (2.0 * u[2] - 1.0),
+                       nbase[2] + rad * (2.0 * u[3] - 1.0)};
+        const double nn = sqrt(dot3(n, n));
+        if (!(nn > 0)) continue;
+        for (int r = 0; r < 3; r++) n[r] /= nn;
+        if (dot3(n, r0) > 0) for (int r = 0; r < 3; r++) n[r] = -n[r];      /* face the camera */
+        if (fabs(dp - c->in.d_min) <= mrel * c->in.d_min || fabs(dp - c->in.d_max) <= mrel * c->in.d_max) *flag = 1;
+        if (dp < c->in.d_min || dp > c->in.d_max) continue;
+        if (grazing(w, n, cu, cv, mrel, flag)) continue;
+        double gt[3];
+        if (!plane_g(w, dp, n, cu, cv, gt)) continue;
+        energy(c, w, s, gt, &t);
+        if (t.flag_energy) *flag = 1;
+        if (ref_out) put3(ref_out + 3 * (8 + k), t.E, t.E_lo, t.E_hi);
+        if (t.E > Ebest) {
+            Ebest = t.E;
+            choice = 8 + k;
+            keep[0] = dp; keep[1] = n[0]; keep[2] = n[1]; keep[3] = n[2];
+        }
+    }
     *Eout = Ebest;
     return choice;
 }
@@ -1011,9 +1056,9 @@ static void iterate_one(orc_ctx *c, int32_t gsp, int32_t item, void *argp)
     int flag = 0;
     double mrel = c->in.margin_rel;
     double *cand = a->cand_out ? a->cand_out + (size_t)item * a->cand_cap * 3 : NULL;
-    double *refo = a->ref_out ? a->ref_out + (size_t)item * 8 * 3 : NULL;
+    double *refo = a->ref_out ? a->ref_out + (size_t)item * ORC_REF_MAX * 3 : NULL;
     if (cand) for (int m = 0; m < a->cand_cap; m++) put3(cand + 3 * m, -INFINITY, -INFINITY, -INFINITY);
-    if (refo) for (int m = 0; m < 8; m++) put3(refo + 3 * m, -INFINITY, -INFINITY, -INFINITY);
+    if (refo) for (int m = 0; m < ORC_REF_MAX; m++) put3(refo + 3 * m, -INFINITY, -INFINITY, -INFINITY);
     if (w->cnt[s] == 0) {
         out[0] = out[1] = out[2] = out[3] = 0;
         goto done;
@@ -1064,7 +1109,7 @@ static void iterate_one(orc_ctx *c, int32_t gsp, int32_t item, void *argp)
     ch1 = -1;
     if (best[0] > 0 && E0 > -INFINITY) {
         double keep[4] = {best[0], best[1], best[2], best[3]};
-        ch1 = refine_step(c, w, s, best[0], E0, keep, &E1, &flag, refo);
+        ch1 = refine_step(c, w, v, s, best[0], best + 1, I, E0, keep, &E1, &flag, refo);
         memcpy(best, keep, sizeof(keep));
     }
     memcpy(out, best, sizeof(best));
@@ -1099,14 +1144,18 @@ void orc_iterate(void *h, int32_t iter, const double *planes_in, const int32_t *
 
 /* Refinement candidates of one superpixel for a given post-propagation depth
  * (used to judge a divergent propagation choice).  out: 8*3 (E, lo, hi). */
-int32_t orc_refine_candidates(void *h, const double *planes_state, int32_t gsp, double dnew, double *out)
+int32_t orc_refine_candidates(void *h, const double *planes_state, int32_t gsp, double dnew, double nx, double ny,
+                              double nz, int32_t iter, double *out)
 {
     orc_ctx *c = h;
     set_state(c, planes_state);
     int v, s, flag = 0;
     locate(c, gsp, &v, &s);
     double keep[4] = {0, 0, 0, 0}, E;
-    int r = refine_step(c, &c->views[v], s, dnew, -INFINITY, keep, &E, &flag, out);
+    const double nb[3] = {nx, ny, nz};
+    for (int m = 0; m < ORC_REF_MAX; m++) put3(out + 3 * m, -INFINITY, -INFINITY, -INFINITY);
+    int r = refine_step(c, &c->views[v], v, s, dnew, nb, iter + c->in.warm_iter_offset, -INFINITY, keep, &E, &flag,
+                        out);
     c->planes = NULL;
     (void)r;
     return flag;

@@ -19,6 +19,7 @@ _SRCS = [_SRC, os.path.join(_HERE, "lfd_fusion_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
+REF_MAX = 32          # refinement candidates per superpixel: 8 triangles + up to 24 perturbation samples
 
 MAXN = 8
 
@@ -54,6 +55,8 @@ class _Input(C.Structure):
         ("lf_index", C.c_int32),
         ("xy_eps", C.c_double),
         ("warm_iter_offset", C.c_int32),
+        ("perturb_samples", C.c_int32),
+        ("perturb_scale", C.c_double),
         ("threads", C.c_int32),
         ("margin_px", C.c_double), ("margin_rel", C.c_double),
     ]
@@ -115,7 +118,7 @@ def _load():
         lib.orc_sweep.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
         lib.orc_iterate.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, i32, vp]
         lib.orc_refine_candidates.restype = i32
-        lib.orc_refine_candidates.argtypes = [vp, vp, i32, f64, vp]
+        lib.orc_refine_candidates.argtypes = [vp, vp, i32, f64, f64, f64, f64, i32, vp]
         lib.orc_score.argtypes = [vp, vp, vp, i32, vp]
         lib.orc_fuse.argtypes = [i32, vp, vp, vp, vp, vp, vp, f64, vp, vp]
         lib.orc_terms_size.restype = i32
@@ -238,6 +241,8 @@ class Oracle:
         inp.sweep_frame = int(params["sweep_frame"])
         inp.seed = int(params["seed"]) & 0xFFFFFFFFFFFFFFFF
         inp.lf_index = int(params["lf_index"])
+        inp.perturb_samples = int(params.get("perturb_samples", 0))
+        inp.perturb_scale = float(params.get("perturb_scale", 0.05))
         inp.xy_eps = float(params["xy_eps"])
         inp.warm_iter_offset = int(params["warm_iter_offset"])
         inp.threads = int(threads or os.cpu_count() or 1)
@@ -334,15 +339,21 @@ class Oracle:
         energy = np.zeros((n, 2))
         flag = np.zeros(n, np.int32)
         cand = np.zeros((n, max(cand_cap, 1), 3)) if cand_cap > 0 else None
-        ref = np.zeros((n, 8, 3))
+        ref = np.zeros((n, REF_MAX, 3))
         self.lib.orc_iterate(self.h, it_index, _p(planes_in), None if it is None else _p(it), n, _p(out),
                              _p(choice), _p(energy), _p(flag), None if cand is None else _p(cand), cand_cap, _p(ref))
         return dict(planes=out, choice=choice, energy=energy, flag=flag, cand=cand, ref=ref)
 
-    def refine_candidates(self, planes_state: np.ndarray, gsp: int, dnew: float) -> np.ndarray:
+    def refine_candidates(self, planes_state: np.ndarray, gsp: int, dnew: float, normal=None,
+                          it_index: int = 1) -> np.ndarray:
+        """Energies (E, lo, hi) of the refinement candidates of superpixel gsp at
+        depth dnew: the 8 ring triangles, then the perturbation samples of the
+        plane (dnew, normal) when the variant is on.  Shape (REF_MAX, 3)."""
         planes_state = np.ascontiguousarray(planes_state, dtype=np.float64).reshape(-1)
-        out = np.zeros((8, 3))
-        self.lib.orc_refine_candidates(self.h, _p(planes_state), int(gsp), float(dnew), _p(out))
+        out = np.zeros((REF_MAX, 3))
+        n = np.zeros(3) if normal is None else np.asarray(normal, dtype=np.float64)
+        self.lib.orc_refine_candidates(self.h, _p(planes_state), int(gsp), float(dnew), float(n[0]), float(n[1]),
+                                       float(n[2]), int(it_index), _p(out))
         return out
 
     def score(self, planes_state: np.ndarray, queries) -> list:

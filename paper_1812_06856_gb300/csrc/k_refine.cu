@@ -183,6 +183,7 @@ struct alignas(16) SpShared {
     SpNb nb[8];
     double cx, cy, rx, ry, rz, rn, grefa;        // centroid, its ray K^-1(c,1), |ray|, anchor g.(ref,1)
     double best_ig;                              // winning candidate (propagation / refinement)
+    double best_dep;                             // depth of the refinement winner
     float bnx, bny, bnz;
     int best_m;
     float k_sig, xy_lo, xy_hi, eta;              // energy constants of the superpixel's light field
@@ -561,10 +562,42 @@ __device__ __noinline__ bool triangle_candidate(const ViewDev &vd, double dnew, 
     nx *= inn; ny *= inn; nz *= inn;
     if (nx * P0x + ny * P0y + nz * P0z > 0.0) { nx = -nx; ny = -ny; nz = -nz; }   // face the camera
     cs.nx[t] = (float)nx; cs.ny[t] = (float)ny; cs.nz[t] = (float)nz;
+    cs.ig[t] = dnew;
     if (!(fabs(nx * sh.rx + ny * sh.ry + nz * sh.rz) >= 0.1 * sh.rn)) return false;   // not grazing
     double tg0 = 0, tg1 = 0, tg2 = 0;
     if (!plane_to_g(vd, dnew, nx, ny, nz, sh.cx, sh.cy, tg0, tg1, tg2)) return false;
     cand_store(cs, t, hyp_prep<DOMAIN>(sh.S, sh, tg0, tg1, tg2));
+    return true;
+}
+
+// Perturbation sample k (flagged variant, not in the paper) of the plane
+// (dnew, n) at iteration I into CandShared slot `slot`: depth scaled by
+// 1 + r (2u - 1) and normal moved by r (2u - 1) per component, r =
+// perturb_scale 2^(1 - I), draws from perturb_u; false when the depth leaves
+// [d_min, d_max] or the plane is grazing.
+template <int DOMAIN>
+__device__ __noinline__ bool perturb_candidate(const ViewDev &vd, double dnew, double n0, double n1, double n2, int I,
+                                               int k, int slot)
+{
+    const SpShared &sh = g_sh[threadIdx.x >> 5];
+    CandShared &cs = g_cs[threadIdx.x >> 5];
+    const double rad = ldexp(vd.perturb_scale, 1 - I);
+    double u[4];
+    for (int j = 0; j < 4; j++) u[j] = perturb_u(vd.seed, vd.lf_index, vd.lv, sh.S.s, I, 4 * k + j);
+    const double dp = dnew * (1.0 + rad * (2.0 * u[0] - 1.0));
+    double nx = n0 + rad * (2.0 * u[1] - 1.0), ny = n1 + rad * (2.0 * u[2] - 1.0), nz = n2 + rad * (2.0 * u[3] - 1.0);
+    const double nn = sqrt(nx * nx + ny * ny + nz * nz);
+    if (!(nn > 0.0)) return false;
+    nx /= nn; ny /= nn; nz /= nn;
+    if (nx * sh.rx + ny * sh.ry + nz * sh.rz > 0.0) { nx = -nx; ny = -ny; nz = -nz; }   // face the camera
+    const double ip = 1.0 / dp;
+    if (!(ip >= vd.inv_dmax && ip <= vd.inv_dmin)) return false;                      // d in [d_min, d_max]
+    if (!(fabs(nx * sh.rx + ny * sh.ry + nz * sh.rz) >= 0.1 * sh.rn)) return false;   // not grazing
+    double tg0 = 0, tg1 = 0, tg2 = 0;
+    if (!plane_to_g(vd, dp, nx, ny, nz, sh.cx, sh.cy, tg0, tg1, tg2)) return false;
+    cand_store(cs, slot, hyp_prep<DOMAIN>(sh.S, sh, tg0, tg1, tg2));
+    cs.nx[slot] = (float)nx; cs.ny[slot] = (float)ny; cs.nz[slot] = (float)nz;
+    cs.ig[slot] = dp;
     return true;
 }
 
@@ -667,7 +700,19 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
     int best_t = -1;
     const double dnew = best_m > 0 ? 1.0 / sh.best_ig : (double)planes_in[gs].x;
     if (Ebest > -INFINITY && dnew > 0.0) {
-        const bool ok = lane < 8 && triangle_candidate<DOMAIN>(vd, dnew, lane);
+        bool ok = false;
+        if (lane < 8) {
+            ok = triangle_candidate<DOMAIN>(vd, dnew, lane);
+        } else if (lane < 8 + vd.perturb_k) {           // flagged variant: random planes around (dnew, n)
+            double n0, n1, n2;
+            if (best_m > 0) {
+                n0 = sh.bnx; n1 = sh.bny; n2 = sh.bnz;
+            } else {
+                const float4 cur = planes_in[gs];
+                n0 = cur.y; n1 = cur.z; n2 = cur.w;
+            }
+            ok = perturb_candidate<DOMAIN>(vd, dnew, n0, n1, n2, ii, lane - 8, lane);
+        }
         cs.ec[lane] = 0.f;
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         __syncwarp();
@@ -684,13 +729,15 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
                     sh.bnx = cs.nx[src];
                     sh.bny = cs.ny[src];
                     sh.bnz = cs.nz[src];
+                    sh.best_dep = cs.ig[src];
                 }
             }
         }
     }
     if (lane == 0) {
         float4 out = planes_in[gs];
-        if (best_t >= 0 || best_m > 0) out = make_float4((float)dnew, sh.bnx, sh.bny, sh.bnz);
+        if (best_t >= 0 || best_m > 0)
+            out = make_float4((float)(best_t >= 0 ? sh.best_dep : dnew), sh.bnx, sh.bny, sh.bnz);
         planes_out[gs] = out;
         if (choice) { choice[2 * gs] = best_m; choice[2 * gs + 1] = best_t; }
         if (energy) { energy[2 * gs] = Eprop; energy[2 * gs + 1] = Ebest; }

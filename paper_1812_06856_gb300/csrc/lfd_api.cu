@@ -281,6 +281,9 @@ lfd_status check_params(lfd_ctx *ctx, const lfd_params *p)
     if (p->depth_domain != 0 && p->depth_domain != 1) return fail(ctx, LFD_ERR_INVALID_ARG, "depth_domain must be 0 or 1");
     if (p->sweep_frame != 0 && p->sweep_frame != 1) return fail(ctx, LFD_ERR_INVALID_ARG, "sweep_frame must be 0 or 1");
     if (p->kernel_size_init < 0) return fail(ctx, LFD_ERR_INVALID_ARG, "kernel_size_init must be >= 0");
+    if (p->perturb_samples < 0 || p->perturb_samples > LFD_MAX_PERTURB || !(p->perturb_scale >= 0) ||
+        !std::isfinite(p->perturb_scale))
+        return fail(ctx, LFD_ERR_INVALID_ARG, "perturb_samples must be 0..%d and perturb_scale >= 0", LFD_MAX_PERTURB);
     return LFD_OK;
 }
 
@@ -357,6 +360,8 @@ void view_params(ViewDev &d, const lfd_params &p, int fmt, int lf)
     d.eta = (float)p.eta;
     d.xy_lo = (float)(1.0 / (1.0 + p.xy_eps));
     d.xy_hi = (float)(1.0 + p.xy_eps);
+    d.perturb_k = p.perturb_samples;
+    d.perturb_scale = p.perturb_scale;
 }
 
 lfd_status ensure_pinned(lfd_ctx *ctx, size_t bytes)
@@ -1036,6 +1041,8 @@ void lfd_params_default(lfd_params *p)
     p->lf_index = 0;
     p->xy_eps = 0.0;
     p->warm_iter_offset = 0;
+    p->perturb_samples = 0;
+    p->perturb_scale = 0.05;
 }
 
 void lfd_batch_options_default(lfd_batch_options *o)

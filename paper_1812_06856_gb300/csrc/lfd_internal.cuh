@@ -22,6 +22,7 @@
 
 #define LFD_MAXN LFD_MAX_NEIGHBOR_VIEWS
 #define LFD_MAX_RADII 64
+#define LFD_MAX_PERTURB 24
 
 namespace lfd {
 
@@ -56,6 +57,8 @@ struct ViewDev {
     float xy_lo, xy_hi;      // X/Y split: inverse domain X iff zeta >= D xy_lo; depth domain X iff z <= D xy_hi
     float col_gain;          // sqrt(k_col): scale of the colours in the rasterised maps
     float dep_gain;          // sqrt(k_sig): scale of their depth values
+    int perturb_k, pad5;     // perturbation samples of the refinement (flagged variant; 0 = off)
+    double perturb_scale;    // their relative radius at I = 1
 };
 
 // view v -> its k-th neighbour view i.  The plane with inverse-depth vector g
@@ -169,6 +172,16 @@ __device__ __forceinline__ double jitter_u(unsigned long long seed, int lf, int 
     unsigned long long key = ((((unsigned long long)lf << 12) + (unsigned long long)v) << 20) + (unsigned long long)s;
     key = (key << 12) + (unsigned long long)k;
     return (double)(splitmix64(seed ^ key) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// uniform [0,1) draw j of the perturbation variant for superpixel s of view v
+// (index within its light field) at iteration I
+__device__ __forceinline__ double perturb_u(unsigned long long seed, int lf, int v, int s, int I, int j)
+{
+    unsigned long long key = ((((unsigned long long)lf << 12) + (unsigned long long)v) << 20) + (unsigned long long)s;
+    key = (key << 7) + (unsigned long long)I;
+    key = (key << 7) + (unsigned long long)j;
+    return (double)(splitmix64((seed ^ 0x5045525455524231ULL) ^ key) >> 11) * (1.0 / 9007199254740992.0);
 }
 
 // Propagation-kernel cell of candidate m (Eq. 4, Fig. 3a): m = 0 own cell,

@@ -49,7 +49,8 @@ class Params(C.Structure):
                 ("eta", C.c_double), ("kernel_size_init", C.c_int32), ("kernel_step_sp", C.c_double),
                 ("max_neighbor_views", C.c_int32), ("depth_domain", C.c_int32), ("jitter", C.c_int32),
                 ("term_mask", C.c_uint32), ("sweep_frame", C.c_int32), ("seed", C.c_uint64),
-                ("lf_index", C.c_int32), ("xy_eps", C.c_double), ("warm_iter_offset", C.c_int32)]
+                ("lf_index", C.c_int32), ("xy_eps", C.c_double), ("warm_iter_offset", C.c_int32),
+                ("perturb_samples", C.c_int32), ("perturb_scale", C.c_double)]
 
 
 class Query(C.Structure):

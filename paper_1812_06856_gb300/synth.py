@@ -539,6 +539,7 @@ def method_params(lf: LightField, **over) -> dict:
         kernel_size_init=0, kernel_step_sp=5.0, max_neighbor_views=8,
         depth_domain=0, jitter=1, term_mask=7, sweep_frame=0,
         seed=(SCENE_SEED_BASE ^ 0x5EED), lf_index=0, xy_eps=0.0, warm_iter_offset=0,
+        perturb_samples=0, perturb_scale=0.05,
     )
     p.update(over)
     return p

@@ -58,6 +58,9 @@ def test_accuracy_over_iterations_terms_and_fusion(lfd, cfg):
                        ("no smoothness E_s", 6)):
         b1, b5 = _bad(run(term_mask=mask).cpu().numpy(), gt)
         rows.append((name, b1, b5))
+    # flagged variant, not in the paper: random plane samples in the refinement step
+    b1, b5 = _bad(run(perturb_samples=16, perturb_scale=0.05).cpu().numpy(), gt)
+    rows.append(("+ 16 perturbation samples", b1, b5))
     depth = run()
     fused = ctx.fuse(depth)
     ctx.synchronize()
@@ -69,4 +72,4 @@ def test_accuracy_over_iterations_terms_and_fusion(lfd, cfg):
         print(f"  {name:26s} {100 * b1:6.2f} % / {100 * b5:6.2f} %")
     # the refinement improves on the sweep, and the full energy is not worse than smoothness alone
     assert curve[-1][2] < curve[0][2]
-    assert rows[0][2] <= rows[-2][2] + 0.02
+    assert rows[0][2] <= rows[2][2] + 0.02

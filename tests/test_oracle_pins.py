@@ -560,3 +560,57 @@ def test_recovery_on_rendered_planes_improves_with_iterations():
     errs = [med(h) for h in hist]
     assert errs[-1] < errs[0]
     assert errs[-1] < 0.01          # median relative inverse-depth error below 1 %
+
+
+# ---------------------------------------------------------------------------
+# flagged variant: random perturbation samples in the refinement step
+# ---------------------------------------------------------------------------
+
+def _cfg1_quarter():
+    lf = synth.make_config(1, scale=0.5)
+    rgb = synth.rgba8_as_float(synth.quantize_rgba8(lf.rgb))
+    return lf, rgb
+
+
+def test_perturbation_with_zero_radius_changes_nothing():
+    """Samples of radius 0 reproduce the propagated plane, which is never
+    strictly better than itself: the iteration equals the paper's."""
+    lf, rgb = _cfg1_quarter()
+    p0 = synth.method_params(lf)
+    pz = synth.method_params(lf, perturb_samples=6, perturb_scale=0.0)
+    o0 = orc.Oracle(*synth.oracle_inputs(lf, rgb), p0)
+    oz = orc.Oracle(*synth.oracle_inputs(lf, rgb), pz)
+    st = o0.sweep()["planes"]
+    r0 = o0.iterate(1, st)
+    rz = oz.iterate(1, st)
+    assert np.array_equal(r0["planes"], rz["planes"])
+    assert np.array_equal(r0["choice"], rz["choice"])
+
+
+def test_perturbation_only_adds_candidates_and_its_winners_are_samples():
+    """Refinement takes the first strictly better candidate in the order
+    triangles, then samples: with samples on, every superpixel's energy after
+    refinement is at least the paper's, equal where no sample wins, and a
+    winning sample (choice >= 8) carries a depth within the radius."""
+    lf, rgb = _cfg1_quarter()
+    scale = 0.05
+    p0 = synth.method_params(lf)
+    pk = synth.method_params(lf, perturb_samples=8, perturb_scale=scale)
+    o0 = orc.Oracle(*synth.oracle_inputs(lf, rgb), p0)
+    ok = orc.Oracle(*synth.oracle_inputs(lf, rgb), pk)
+    st = o0.sweep()["planes"]
+    r0 = o0.iterate(2, st)
+    rk = ok.iterate(2, st)
+    assert np.all(rk["energy"][:, 1] >= r0["energy"][:, 1])
+    won = rk["choice"][:, 1] >= 8
+    assert won.any()
+    same = ~won
+    assert np.array_equal(rk["energy"][same, 1], r0["energy"][same, 1])
+    # propagation is untouched
+    assert np.array_equal(rk["choice"][:, 0], r0["choice"][:, 0])
+    # the sample's depth lies within the iteration-2 radius of the propagated depth
+    rad = scale * 2.0 ** (1 - 2)
+    prop_d = np.where(rk["choice"][:, 0] > 0, np.nan, st[:, 0])      # current plane kept by propagation
+    keep = won & np.isfinite(prop_d)
+    rel = np.abs(rk["planes"][keep, 0] / prop_d[keep] - 1.0)
+    assert np.all(rel <= rad * (1 + 1e-12))
