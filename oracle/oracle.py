@@ -15,7 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lfd_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "lfd_fusion_oracle.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "lfd_fusion_oracle.c"), os.path.join(_HERE, "lfd_slic_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
@@ -121,6 +121,11 @@ def _load():
         lib.orc_refine_candidates.argtypes = [vp, vp, i32, f64, f64, f64, f64, i32, vp]
         lib.orc_score.argtypes = [vp, vp, vp, i32, vp]
         lib.orc_fuse.argtypes = [i32, vp, vp, vp, vp, vp, vp, f64, vp, vp]
+        lib.orc_rgb_to_lab.argtypes = [vp, vp]
+        lib.orc_slic_seeds.argtypes = [i32, i32, vp, i32, i32, vp]
+        lib.orc_slic_assign.argtypes = [i32, i32, vp, i32, i32, vp, f64, vp, vp]
+        lib.orc_slic_update.argtypes = [i32, i32, vp, i32, i32, vp, vp, vp]
+        lib.orc_slic.argtypes = [i32, i32, vp, i32, i32, f64, i32, vp, vp]
         lib.orc_terms_size.restype = i32
         lib.orc_query_size.restype = i32
         lib.orc_input_size.restype = i32
@@ -176,6 +181,53 @@ def fuse(K, R, t, depths, tau: float = 0.01):
     pin, pout, pfl = arr(ds), arr(outs), arr(flags)
     lib.orc_fuse(V, _p(K), _p(R), _p(t), _p(W), _p(H), pin, float(tau), pout, pfl)
     return outs, flags
+
+
+def rgb_to_lab(rgb) -> np.ndarray:
+    rgb = np.ascontiguousarray(rgb, dtype=np.float64).reshape(3)
+    out = np.zeros(3)
+    _load().orc_rgb_to_lab(_p(rgb), _p(out))
+    return out
+
+
+def slic_seeds(rgb: np.ndarray, GW: int, GH: int) -> np.ndarray:
+    """Initial SLIC centres {L, a, b, x, y} per grid cell (lfd_slic_oracle.c)."""
+    rgb = np.ascontiguousarray(rgb, dtype=np.float64)
+    H, W = rgb.shape[:2]
+    c = np.zeros((GH * GW, 5))
+    _load().orc_slic_seeds(W, H, _p(rgb), GW, GH, _p(c))
+    return c
+
+
+def slic_assign(rgb: np.ndarray, GW: int, GH: int, centres: np.ndarray, m: float):
+    """One SLIC assignment: (labels (H, W) int32, near-tie flags (H, W))."""
+    rgb = np.ascontiguousarray(rgb, dtype=np.float64)
+    H, W = rgb.shape[:2]
+    centres = np.ascontiguousarray(centres, dtype=np.float64)
+    lab = np.zeros((H, W), np.int32)
+    fl = np.zeros((H, W), np.uint8)
+    _load().orc_slic_assign(W, H, _p(rgb), GW, GH, _p(centres), float(m), _p(lab), _p(fl))
+    return lab, fl
+
+
+def slic_update(rgb: np.ndarray, GW: int, GH: int, labels: np.ndarray, centres: np.ndarray) -> np.ndarray:
+    rgb = np.ascontiguousarray(rgb, dtype=np.float64)
+    H, W = rgb.shape[:2]
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    centres = np.ascontiguousarray(centres, dtype=np.float64)
+    out = np.zeros_like(centres)
+    _load().orc_slic_update(W, H, _p(rgb), GW, GH, _p(labels), _p(centres), _p(out))
+    return out
+
+
+def slic(rgb: np.ndarray, GW: int, GH: int, m: float = 10.0, iterations: int = 10):
+    """Full SLIC (seeds, iterations x (assign, update), final assign): (labels, centres)."""
+    rgb = np.ascontiguousarray(rgb, dtype=np.float64)
+    H, W = rgb.shape[:2]
+    lab = np.zeros((H, W), np.int32)
+    c = np.zeros((GH * GW, 5))
+    _load().orc_slic(W, H, _p(rgb), GW, GH, float(m), int(iterations), _p(lab), _p(c))
+    return lab, c
 
 
 def terms_to_dict(t: Terms, n: int) -> dict:
