@@ -394,6 +394,22 @@ def run_ours(args):
                       "changed_fraction": float((fused != depth).float().mean().item())}
     del fused
 
+    # GPU SLIC (the segmentation before Section III-A) of the frame's views,
+    # 10 iterations, one superpixel per grid cell of the frame: timed beside
+    # the step like the fusion
+    for _ in range(2):
+        ctx.slic(views, lf.GW, lf.GH, 10.0, iterations=10, stream=stream)
+    sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    for a, b in sev:
+        flush.fill_(3)
+        a.record(stream)
+        ctx.slic(views, lf.GW, lf.GH, 10.0, iterations=10, stream=stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    s_ms = float(np.mean([a.elapsed_time(b) for a, b in sev]))
+    line["slic"] = {"ms": s_ms, "ms_per_view": s_ms / V, "iterations": 10, "compactness": 10.0,
+                    "cells": [int(lf.GW), int(lf.GH)]}
+
     # end to end through the host-memory entry point
     if not args.no_e2e:
         vh = views.cpu().pin_memory()

@@ -238,6 +238,30 @@ lfd_status lfd_estimate(lfd_ctx *ctx, const lfd_lightfield *lf, const lfd_params
 lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const lfd_params *p,
                              float *const *planes_out_host, float *const *depth_out_host, void *stream);
 
+/* ---- SLIC superpixels (step before the hot path) ----------------------- */
+
+/* SLIC segmentation (Achanta et al. 2012; the paper segments every view with
+ * a GPU SLIC before Section III-A) into label maps the rest of the path takes
+ * as they are: label = cy * grid_w + cx of the winning seed cell.
+ * CIELAB (sRGB companding, D65); one seed per cell of the grid whose
+ * boundaries are at round(k W / grid_w) (half up), at the cell centre with the
+ * colour of its nearest pixel; each iteration assigns every pixel to the
+ * nearest of the 3x3 seed cells around its own cell by
+ * D^2 = |dLab|^2 + (compactness / S)^2 |dxy|^2, S = sqrt(W H / (grid_w grid_h))
+ * (ties to the first cell in row-major order), then moves each centre to the
+ * mean of its pixels; a final assignment writes the labels.  No connectivity
+ * post-processing.
+ *   views, view_pitch_bytes (nullable = packed), width, height, grid_w,
+ *   grid_h: arrays [n] (host); images and labels_out[v] (int32 H*W) on the
+ *   device.  centres_in / centres_out (nullable; entries float[grid_w*grid_h*5]
+ *   {L, a, b, x, y} on the device): start from given centres instead of the
+ *   seeds / receive the centres the final assignment used.
+ * Scratch is allocated in the context on first use.  Asynchronous. */
+lfd_status lfd_slic(lfd_ctx *ctx, int32_t n, const void *const *views, const int64_t *view_pitch_bytes, int32_t fmt,
+                    const int32_t *width, const int32_t *height, const int32_t *grid_w, const int32_t *grid_h,
+                    double compactness, int32_t iterations, int32_t *const *labels_out,
+                    const float *const *centres_in, float *const *centres_out, void *stream);
+
 /* ---- depth fusion (step after the hot path) ---------------------------- */
 
 /* Stability-based depth fusion (Section III-D) of one depth map per bound

@@ -27,7 +27,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define SLIC_MARGIN 1e-6   /* relative gap between the two smallest D^2 below which a pixel is flagged */
+#define SLIC_MARGIN 1e-4   /* relative gap between the two smallest D^2 below which a pixel is flagged */
 
 static double srgb_to_linear(double c)
 {

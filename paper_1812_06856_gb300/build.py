@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblfdepth.so")
-SOURCES = ["lfd_api.cu", "k_superpixels.cu", "k_sweep.cu", "k_refine.cu", "k_noalloc.cu", "lfd_server.cu", "k_fuse.cu"]
+SOURCES = ["lfd_api.cu", "k_superpixels.cu", "k_sweep.cu", "k_refine.cu", "k_noalloc.cu", "lfd_server.cu", "k_fuse.cu", "k_slic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-diag-suppress", "1444"]

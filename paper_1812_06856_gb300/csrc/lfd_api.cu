@@ -226,6 +226,8 @@ struct lfd_ctx {
     PinnedRing dtab;                 // depth-output pointer tables
     PinnedRing ftab;                 // fusion tables
     std::vector<lfd_camera> cams;    // cameras of the bound views (global order)
+    void *d_slic = nullptr;          // SLIC scratch (CIELAB image, centres)
+    size_t slic_cap = 0;
     unsigned *d_zbuf = nullptr;      // fusion z-buffers (one light field at a time)
     size_t zbuf_cap = 0;
     void *d_ftab = nullptr;
@@ -1101,6 +1103,7 @@ lfd_status lfd_destroy(lfd_ctx *ctx)
     ctx->dtab.release();
     ctx->ftab.release();
     if (ctx->d_zbuf) cudaFree(ctx->d_zbuf);
+    if (ctx->d_slic) cudaFree(ctx->d_slic);
     if (ctx->d_ftab) cudaFree(ctx->d_ftab);
     if (ctx->h_bdepth) cudaFreeHost(ctx->h_bdepth);
     if (ctx->ev_bdepth) cudaEventDestroy(ctx->ev_bdepth);
@@ -1491,6 +1494,56 @@ lfd_status lfd_fuse(lfd_ctx *ctx, const float *const *depth_in, float *const *de
         a.mats = (const float *)(d + o_mats);
         a.zbuf = ctx->d_zbuf;
         LFD_CUDA(traced(ctx, LFD_STAGE_FUSION, st, [&] { return launch_fuse(a, zw, max_px, st); }));
+    }
+    return LFD_OK;
+}
+
+
+lfd_status lfd_slic(lfd_ctx *ctx, int32_t n, const void *const *views, const int64_t *view_pitch_bytes, int32_t fmt,
+                    const int32_t *width, const int32_t *height, const int32_t *grid_w, const int32_t *grid_h,
+                    double compactness, int32_t iterations, int32_t *const *labels_out,
+                    const float *const *centres_in, float *const *centres_out, void *stream)
+{
+    if (!ctx) return LFD_ERR_INVALID_ARG;
+    ctx->err.clear();
+    lfd_status s;
+    if ((s = set_device(ctx)) != LFD_OK) return s;
+    const int tb = texel_bytes(fmt);
+    if (n < 1 || !views || !width || !height || !grid_w || !grid_h || !labels_out || tb == 0)
+        return fail(ctx, LFD_ERR_INVALID_ARG, "lfd_slic: bad arguments");
+    if (!(compactness > 0.0) || iterations < 0 || iterations > 1000)
+        return fail(ctx, LFD_ERR_INVALID_ARG, "compactness must be > 0 and iterations 0..1000");
+    size_t need = 0;
+    for (int v = 0; v < n; v++) {
+        if (width[v] < 1 || height[v] < 1 || width[v] > LFD_MAX_DIM || height[v] > LFD_MAX_DIM || grid_w[v] < 1 ||
+            grid_h[v] < 1 || grid_w[v] > width[v] || grid_h[v] > height[v] || !views[v] || !labels_out[v])
+            return fail(ctx, LFD_ERR_INVALID_ARG, "lfd_slic: view %d: bad size, grid or pointer", v);
+        const long long pitch = view_pitch_bytes && view_pitch_bytes[v] ? view_pitch_bytes[v] : (long long)width[v] * tb;
+        if (pitch < (long long)width[v] * tb || pitch % tb)
+            return fail(ctx, LFD_ERR_INVALID_ARG, "lfd_slic: view %d: bad pitch", v);
+        const size_t b = align_up(16 * (size_t)width[v] * height[v], 256) + 2 * align_up(20 * (size_t)grid_w[v] * grid_h[v], 256);
+        need = std::max(need, b);
+    }
+    if ((s = ensure_dev(ctx, &ctx->d_slic, &ctx->slic_cap, need)) != LFD_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int v = 0; v < n; v++) {
+        SlicView sv;
+        sv.W = width[v];
+        sv.H = height[v];
+        sv.GW = grid_w[v];
+        sv.GH = grid_h[v];
+        sv.fmt = fmt;
+        sv.pad = 0;
+        sv.pitch = view_pitch_bytes && view_pitch_bytes[v] ? view_pitch_bytes[v] : (long long)width[v] * tb;
+        sv.img = views[v];
+        char *base = (char *)ctx->d_slic;
+        const size_t o_c = align_up(16 * (size_t)sv.W * sv.H, 256), sz_c = align_up(20 * (size_t)sv.GW * sv.GH, 256);
+        sv.lab = (float4 *)base;
+        sv.centres = (float *)(base + o_c);
+        sv.centres2 = (float *)(base + o_c + sz_c);
+        sv.labels = labels_out[v];
+        LFD_CUDA(launch_slic(sv, centres_in ? centres_in[v] : nullptr, iterations, (float)compactness,
+                             centres_out ? centres_out[v] : nullptr, st));
     }
     return LFD_OK;
 }

@@ -125,6 +125,16 @@ struct FuseArgs {
     unsigned *zbuf;
 };
 
+// one view of a SLIC segmentation
+struct SlicView {
+    int W, H, GW, GH, fmt, pad;
+    long long pitch;                 // bytes per image row
+    const void *img;
+    float4 *lab;                     // [W*H] CIELAB of the view (scratch)
+    int *labels;                     // [W*H] output
+    float *centres, *centres2;       // [GW*GH][5] {L, a, b, x, y} (scratch, ping-pong)
+};
+
 // ---------------------------------------------------------------------------
 // small device helpers
 // ---------------------------------------------------------------------------
@@ -225,6 +235,8 @@ cudaError_t launch_propagate(const Workspace &w, const Consts &c, const LaunchCf
                              const float4 *planes_in, float4 *planes_out, int *choice, float *energy,
                              cudaStream_t st);
 cudaError_t launch_fuse(const FuseArgs &a, long long zbuf_words, int max_px, cudaStream_t st);
+cudaError_t launch_slic(const SlicView &s, const float *centres_in, int iterations, float m, float *centres_out,
+                        cudaStream_t st);
 cudaError_t launch_score(const Workspace &w, const Consts &c, const float4 *planes_state, int nq, const lfd_query *q,
                          float *out, cudaStream_t st);
 }  // namespace lfd

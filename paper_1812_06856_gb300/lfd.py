@@ -125,6 +125,7 @@ def load(build_if_missing: bool = True):
     lib.lfd_launch_config.argtypes = [vp, P(i32)]
     lib.lfd_workspace_required.argtypes = [i32, P(LightFieldC), P(C.c_uint64)]
     lib.lfd_fuse.argtypes = [vp, P(vp), P(vp), C.c_double, vp]
+    lib.lfd_slic.argtypes = [vp, i32, P(vp), vp, i32, vp, vp, vp, vp, C.c_double, i32, P(vp), P(vp), P(vp), vp]
     lib.lfd_server_create.argtypes = [P(vp), i32, C.c_uint64, i32]
     lib.lfd_server_destroy.argtypes = [vp]
     lib.lfd_server_last_error.argtypes = [vp]
@@ -139,7 +140,7 @@ def load(build_if_missing: bool = True):
     for name in ("lfd_create", "lfd_destroy", "lfd_set_input", "lfd_num_superpixels", "lfd_plane_sweep",
                  "lfd_rasterize", "lfd_iterate", "lfd_estimate", "lfd_estimate_host", "lfd_synchronize",
                  "lfd_counters", "lfd_score", "lfd_get_superpixels", "lfd_neighbor_views", "lfd_profile_enable",
-                 "lfd_profile_read", "lfd_estimate_batch", "lfd_launch_config", "lfd_workspace_required", "lfd_fuse",
+                 "lfd_profile_read", "lfd_estimate_batch", "lfd_launch_config", "lfd_workspace_required", "lfd_fuse", "lfd_slic",
                  "lfd_server_create", "lfd_server_destroy", "lfd_server_configure", "lfd_server_submit",
                  "lfd_server_poll", "lfd_server_export_state", "lfd_server_import_state"):
         getattr(lib, name).restype = i32
@@ -461,6 +462,25 @@ class Context:
         self._keep = [self._keep, pin, pout, maps, outs]
         self._check(self.lib.lfd_fuse(self.h, pin, pout, float(tau), _stream(stream)), "lfd_fuse")
         return out
+
+    def slic(self, views: torch.Tensor, GW: int, GH: int, compactness: float = 10.0, iterations: int = 10,
+             centres_in: torch.Tensor | None = None, want_centres: bool = False, stream=None):
+        """SLIC label maps (lfd_slic) of views (V, H, W, 4) on the device: returns
+        labels (V, H, W) int32 and, with want_centres, centres (V, GW*GH, 5)."""
+        V, H, W = int(views.shape[0]), int(views.shape[1]), int(views.shape[2])
+        fmt = _DTYPE_FMT[views.dtype]
+        labels = torch.zeros((V, H, W), dtype=torch.int32, device=views.device)
+        cout = torch.zeros((V, GW * GH, 5), dtype=torch.float32, device=views.device) if want_centres else None
+        vptr = _ptr_array([views[v].data_ptr() for v in range(V)])
+        lptr = _ptr_array([labels[v].data_ptr() for v in range(V)])
+        ci = _ptr_array([centres_in[v].data_ptr() for v in range(V)]) if centres_in is not None else None
+        co = _ptr_array([cout[v].data_ptr() for v in range(V)]) if cout is not None else None
+        ints = lambda x: (C.c_int32 * V)(*([int(x)] * V))
+        w, h, gw, gh = ints(W), ints(H), ints(GW), ints(GH)
+        self._keep = [self._keep, vptr, lptr, ci, co, w, h, gw, gh, views, centres_in]
+        self._check(self.lib.lfd_slic(self.h, V, vptr, None, fmt, w, h, gw, gh, float(compactness), int(iterations),
+                                      lptr, ci, co, _stream(stream)), "lfd_slic")
+        return (labels, cout) if want_centres else labels
 
     def launch_config(self) -> dict:
         out = (C.c_int32 * 4)()
