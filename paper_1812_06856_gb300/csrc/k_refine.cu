@@ -42,6 +42,40 @@ constexpr int PROP_WARPS = 4;
 constexpr int SLOTS_MAX = 10;   // pixel slots per lane staged in shared memory (320 pixels per warp)
 
 
+// FP64 reciprocal and reciprocal square root by Newton-Raphson refinement of
+// the FP32 hardware estimates (two steps each: y += y (1 - x y) and
+// y += y (1/2 - x y^2 / 2)), which leaves ~1 ulp; outside FP32's normal range
+// the IEEE operations.  Short code on the low-rate FP64 pipe.
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ double rcp64(double x)
+{
+    const float a = fabsf((float)x);
+    if (!(a >= 1e-30f && a <= 1e30f)) return 1.0 / x;
+    double y = (double)rcp_approx((float)x);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+__device__ __forceinline__ double rsqrt64(double x)
+{
+    const float a = (float)x;
+    if (!(a >= 1e-30f && a <= 1e30f)) return 1.0 / sqrt(x);
+    double y = (double)rsqrt_approx(a);
+    const double h = 0.5 * x;
+    double e = fma(-h * y, y, 0.5);
+    y = fma(y, e, y);
+    e = fma(-h * y, y, 0.5);
+    return fma(y, e, y);
+}
+
 // ---------------------------------------------------------------------------
 // plane coefficients of a state: g with 1/depth(p) = g . (p,1)
 // ---------------------------------------------------------------------------
@@ -57,9 +91,10 @@ __device__ __forceinline__ bool plane_to_g(const ViewDev &vd, double d, double n
     const double rz = K[6] * cx + K[7] * cy + K[8];
     const double rho = d * (nx * rx + ny * ry + nz * rz);       // n . X_c
     if (!(fabs(rho) > 0.0) || !isfinite(rho)) return false;
-    g0 = (K[0] * nx + K[3] * ny + K[6] * nz) / rho;              // K^-T n / rho
-    g1 = (K[1] * nx + K[4] * ny + K[7] * nz) / rho;
-    g2 = (K[2] * nx + K[5] * ny + K[8] * nz) / rho;
+    const double ir = rcp64(rho);
+    g0 = (K[0] * nx + K[3] * ny + K[6] * nz) * ir;               // K^-T n / rho
+    g1 = (K[1] * nx + K[4] * ny + K[7] * nz) * ir;
+    g2 = (K[2] * nx + K[5] * ny + K[8] * nz) * ir;
     return isfinite(g0) && isfinite(g1) && isfinite(g2);
 }
 
@@ -167,6 +202,8 @@ struct alignas(16) SpNb {
     double Px, Py, Pz;                   // its centroid point d K^-1 (c,1) (Fig. 3b vertices)
     float w;                             // colour weight exp(-(a_j - min a))
     int ok;
+    float fdx, fdy;                      // c_j - c (own centroid), FP32
+    float finvd, fd;                     // invd, d in FP32
 };
 
 // the superpixel a warp works on (identical in every lane)
@@ -187,6 +224,7 @@ struct alignas(16) SpShared {
     float bnx, bny, bnz;
     int best_m;
     float k_sig, xy_lo, xy_hi, eta;              // energy constants of the superpixel's light field
+    float rdx, rdy;                              // ref - c (anchor pixel minus centroid)
     int term_mask;
 };
 
@@ -221,9 +259,12 @@ struct ViewK {
     const float4 *map;
 };
 
-// E_s (Eq. 5-7) of plane g for this lane; neighbours in ring order.
+// E_s (Eq. 5-7) of plane g for this lane; neighbours in ring order.  The
+// plane's inverse depth at c_j is taken relative to its value igc at the own
+// centroid, g . (c_j,1) = igc + g0 dx_j + g1 dy_j, so that FP32 suffices: the
+// offsets are a few superpixel pitches and no large terms cancel.
 template <int DOMAIN>
-__device__ __forceinline__ float smoothness(const SpShared &sh, float sum_w, double g0, double g1, double g2)
+__device__ __forceinline__ float smoothness(const SpShared &sh, float sum_w, float g0, float g1, float igc)
 {
     if (!(sum_w > 0.f)) return 1.f;
     float num = 0.f;
@@ -231,30 +272,36 @@ __device__ __forceinline__ float smoothness(const SpShared &sh, float sum_w, dou
     for (int j = 0; j < 8; j++) {
         const SpNb &nb = sh.nb[j];
         if (!nb.ok) continue;
-        const double ext = g0 * nb.cx + g1 * nb.cy + g2;         // plane's inverse depth at c_j
+        const float dext = fmaf(g0, nb.fdx, g1 * nb.fdy);          // g . (c_j,1) - igc
         float dl;
         bool has = true;
         if (DOMAIN == 0) {
-            dl = (float)(nb.invd - ext);
+            dl = (nb.finvd - igc) - dext;
         } else {
-            has = ext > 0.0;
-            dl = has ? (float)(nb.d - 1.0 / ext) : 0.f;
+            const float ext = igc + dext;
+            has = ext > 0.f;
+            dl = has ? nb.fd - rcp_approx(ext) : 0.f;
         }
         if (has) num += nb.w * ex2_approx(-dl * dl * sh.k_sig);
     }
-    return num / sum_w;
+    return num * rcp_approx(sum_w);
 }
 
+// FP32 form of plane g whose inverse depth at the own centroid is igc
+// (g . (c,1), FP64): everything relative to igc, so the only FP64 step left
+// is the anchored difference igc - g_a . (ref,1).  The low-rate FP64 pipe of
+// this GPU is kept for the few steps that need it.
 template <int DOMAIN>
-__device__ __noinline__ HypF hyp_prep(const WarpSP &S, const SpShared &sh, double g0, double g1, double g2)
+__device__ __noinline__ HypF hyp_prep(const WarpSP &S, const SpShared &sh, double g0, double g1, double igc)
 {
     HypF h;
-    const double gref = g0 * S.ref.x + g1 * S.ref.y + g2;
-    h.g0 = (float)g0;
-    h.g1 = (float)g1;
-    h.gr = (float)gref;
-    h.dgr = (float)(gref - sh.grefa);
-    h.es = smoothness<DOMAIN>(sh, S.sum_w, g0, g1, g2);
+    const float g0f = (float)g0, g1f = (float)g1, igf = (float)igc;
+    const float dref = fmaf(g0f, sh.rdx, g1f * sh.rdy);           // g . (ref,1) - igc
+    h.g0 = g0f;
+    h.g1 = g1f;
+    h.gr = igf + dref;
+    h.dgr = (float)(igc - sh.grefa) + dref;
+    h.es = smoothness<DOMAIN>(sh, S.sum_w, g0f, g1f, igf);
     return h;
 }
 
@@ -319,15 +366,18 @@ __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du
 // project the superpixel to nearly the same region of a neighbour view, so
 // that region's map texels are reused from L1 across the batch.  SL pixel
 // slots per lane; unless MASK_ALL, every slot but the last is full
-// (n > 32 (SL - 1)).  With `rec` (one candidate), lane 0 writes the per-view
-// terms of lfd_score.
-template <int DOMAIN, int SL, bool MASK_ALL = false>
+// (n > 32 (SL - 1)).  With REC (one candidate), lane 0 writes the per-view
+// terms of lfd_score to `rec`.  Lane c keeps candidate c's running sum in a
+// register (the reduced terms are identical in every lane), so the loop has
+// no divergent store.
+template <int DOMAIN, int SL, bool MASK_ALL = false, bool REC = false>
 __device__ __noinline__ void view_terms(const Workspace &w, unsigned mask, float *rec)
 {
     const int lane = threadIdx.x & 31;
     const SpShared &sh = g_sh[threadIdx.x >> 5];
     CandShared &cs = g_cs[threadIdx.x >> 5];
     const WarpSP S = sh.S;
+    float ec = cs.ec[lane];
     for (int k = 0; k < S.nnb; k++) {
         const SpView &sv = sh.view[k];
         unsigned mm = mask;
@@ -379,22 +429,21 @@ __device__ __noinline__ void view_terms(const Workspace &w, unsigned mask, float
             const float Si = cnt > 0 ? sw * rcp_approx((float)cnt) : 0.f;                      // Eq. 9
             const float Vi = (cnt > 0 && nx > 0) ? Si * (sg * rcp_approx((float)nx)) : 0.f;    // Eq. 10
             const float Oi = (ny > 0 && (sh.term_mask & 4)) ? sh.eta * (1.f - S.minw) : 0.f;   // Eq. 11
-            if (lane == 0) {
-                cs.ec[src] += Vi + Oi;
-                if (rec) {
-                    float *r = rec + LFD_TERMS_HEAD + k * LFD_TERMS_PER_VIEW;
-                    r[0] = Si; r[1] = Vi; r[2] = Oi; r[3] = (float)cnt; r[4] = (float)nx; r[5] = (float)ny;
-                }
+            ec += lane == src ? Vi + Oi : 0.f;
+            if (REC && lane == 0) {
+                float *r = rec + LFD_TERMS_HEAD + k * LFD_TERMS_PER_VIEW;
+                r[0] = Si; r[1] = Vi; r[2] = Oi; r[3] = (float)cnt; r[4] = (float)nx; r[5] = (float)ny;
             }
         }
     }
+    cs.ec[lane] = ec;
     __syncwarp();
 }
 
 // E = E_c E_s (Eq. 3, Eq. 8) of candidate src after view_terms
 __device__ __forceinline__ float cand_energy(const SpShared &sh, const CandShared &cs, int nnb, int src)
 {
-    const float Ec = nnb > 0 ? cs.ec[src] / (float)nnb : 0.f;
+    const float Ec = nnb > 0 ? cs.ec[src] * rcp_approx((float)nnb) : 0.f;
     return ((sh.term_mask & 2) ? Ec : 1.f) * ((sh.term_mask & 1) ? cs.es[src] : 1.f);
 }
 
@@ -431,8 +480,11 @@ __device__ bool setup_sp(const Workspace &w, const float4 *planes_in, int gs, in
         sh.eta = vd.eta;
         sh.term_mask = vd.term_mask;
         sh.cx = cc.x; sh.cy = cc.y;
+        sh.rdx = (float)(S.ref.x - cc.x);
+        sh.rdy = (float)(S.ref.y - cc.y);
         sh.rx = rx; sh.ry = ry; sh.rz = rz;
-        sh.rn = sqrt(rx * rx + ry * ry + rz * rz);
+        const double rn2 = rx * rx + ry * ry + rz * rz;
+        sh.rn = rn2 * rsqrt64(rn2);
         sh.grefa = grefa;
     }
 
@@ -443,6 +495,7 @@ __device__ bool setup_sp(const Workspace &w, const float4 *planes_in, int gs, in
         nb.invd = nb.d = nb.cx = nb.cy = nb.Px = nb.Py = nb.Pz = 0.0;
         nb.ok = 0;
         nb.w = 0.f;
+        nb.fdx = nb.fdy = nb.finvd = nb.fd = 0.f;
         int dx, dy;
         ring_dir(lane, dx, dy);
         const int x = S.gx + dx, y = S.gy + dy;
@@ -457,9 +510,13 @@ __device__ bool setup_sp(const Workspace &w, const float4 *planes_in, int gs, in
                     a = fmaf(dr, dr, fmaf(dg, dg, db * db)) * vd.k_col;
                     const double2 c2 = w.sp_cen[j];
                     nb.d = pj.x;
-                    nb.invd = 1.0 / (double)pj.x;
+                    nb.invd = rcp64((double)pj.x);
                     nb.cx = c2.x;
                     nb.cy = c2.y;
+                    nb.fdx = (float)(c2.x - cc.x);
+                    nb.fdy = (float)(c2.y - cc.y);
+                    nb.finvd = (float)nb.invd;
+                    nb.fd = pj.x;
                     nb.Px = nb.d * (Ki[0] * c2.x + Ki[1] * c2.y + Ki[2]);
                     nb.Py = nb.d * (Ki[3] * c2.x + Ki[4] * c2.y + Ki[5]);
                     nb.Pz = nb.d * (Ki[6] * c2.x + Ki[7] * c2.y + Ki[8]);
@@ -489,14 +546,14 @@ __device__ bool setup_sp(const Workspace &w, const float4 *planes_in, int gs, in
         const double hx = fma(pd.q[0], grefa, pr0), hy = fma(pd.q[1], grefa, pr1), hw = fma(pd.q[2], grefa, pr2);
         double xa = 0.0, ya = 0.0;
         if (hw > 0.0) {
-            const double ihw = 1.0 / hw;
+            const double ihw = rcp64(hw);
             xa = floor(hx * ihw);
             ya = floor(hy * ihw);
             xa = fmin(fmax(xa, -1048576.0), 1048576.0);
             ya = fmin(fmax(ya, -1048576.0), 1048576.0);
         }
         // rows scaled so that gp / Nw (or Nw / gp) carries sqrt(k_sig), see energy_sample
-        const double rs = DOMAIN == 0 ? 1.0 / (double)vd.dep_gain : (double)vd.dep_gain;
+        const double rs = DOMAIN == 0 ? rcp64((double)vd.dep_gain) : (double)vd.dep_gain;
         SpView sv;
         sv.hw_a = (float)(hw * rs);
         sv.qw = (float)(pd.q[2] * rs);
@@ -544,7 +601,7 @@ __device__ bool setup_sp(const Workspace &w, const float4 *planes_in, int gs, in
 // facing the camera; false for a missing vertex, a degenerate or a grazing
 // triangle.  The plane goes to the warp's CandShared slot t.
 template <int DOMAIN>
-__device__ __noinline__ bool triangle_candidate(const ViewDev &vd, double dnew, int t)
+__device__ __noinline__ bool triangle_candidate(const ViewDev &vd, double dnew, double ignew, int t)
 {
     const SpShared &sh = g_sh[threadIdx.x >> 5];
     CandShared &cs = g_cs[threadIdx.x >> 5];
@@ -558,7 +615,7 @@ __device__ __noinline__ bool triangle_candidate(const ViewDev &vd, double dnew, 
     const double nn2 = nx * nx + ny * ny + nz * nz;
     const double l12 = (e1x * e1x + e1y * e1y + e1z * e1z) * (e2x * e2x + e2y * e2y + e2z * e2z);
     if (!(nn2 > 0.0 && nn2 >= 1e-24 * l12)) return false;               // |n| >= 1e-12 |e1| |e2|
-    const double inn = 1.0 / sqrt(nn2);
+    const double inn = rsqrt64(nn2);
     nx *= inn; ny *= inn; nz *= inn;
     if (nx * P0x + ny * P0y + nz * P0z > 0.0) { nx = -nx; ny = -ny; nz = -nz; }   // face the camera
     cs.nx[t] = (float)nx; cs.ny[t] = (float)ny; cs.nz[t] = (float)nz;
@@ -566,7 +623,7 @@ __device__ __noinline__ bool triangle_candidate(const ViewDev &vd, double dnew, 
     if (!(fabs(nx * sh.rx + ny * sh.ry + nz * sh.rz) >= 0.1 * sh.rn)) return false;   // not grazing
     double tg0 = 0, tg1 = 0, tg2 = 0;
     if (!plane_to_g(vd, dnew, nx, ny, nz, sh.cx, sh.cy, tg0, tg1, tg2)) return false;
-    cand_store(cs, t, hyp_prep<DOMAIN>(sh.S, sh, tg0, tg1, tg2));
+    cand_store(cs, t, hyp_prep<DOMAIN>(sh.S, sh, tg0, tg1, ignew));   // g . (c,1) = 1 / dnew
     return true;
 }
 
@@ -586,16 +643,17 @@ __device__ __noinline__ bool perturb_candidate(const ViewDev &vd, double dnew, d
     for (int j = 0; j < 4; j++) u[j] = perturb_u(vd.seed, vd.lf_index, vd.lv, sh.S.s, I, 4 * k + j);
     const double dp = dnew * (1.0 + rad * (2.0 * u[0] - 1.0));
     double nx = n0 + rad * (2.0 * u[1] - 1.0), ny = n1 + rad * (2.0 * u[2] - 1.0), nz = n2 + rad * (2.0 * u[3] - 1.0);
-    const double nn = sqrt(nx * nx + ny * ny + nz * nz);
-    if (!(nn > 0.0)) return false;
-    nx /= nn; ny /= nn; nz /= nn;
+    const double nn2 = nx * nx + ny * ny + nz * nz;
+    if (!(nn2 > 0.0)) return false;
+    const double inn = rsqrt64(nn2);
+    nx *= inn; ny *= inn; nz *= inn;
     if (nx * sh.rx + ny * sh.ry + nz * sh.rz > 0.0) { nx = -nx; ny = -ny; nz = -nz; }   // face the camera
-    const double ip = 1.0 / dp;
+    const double ip = rcp64(dp);
     if (!(ip >= vd.inv_dmax && ip <= vd.inv_dmin)) return false;                      // d in [d_min, d_max]
     if (!(fabs(nx * sh.rx + ny * sh.ry + nz * sh.rz) >= 0.1 * sh.rn)) return false;   // not grazing
     double tg0 = 0, tg1 = 0, tg2 = 0;
     if (!plane_to_g(vd, dp, nx, ny, nz, sh.cx, sh.cy, tg0, tg1, tg2)) return false;
-    cand_store(cs, slot, hyp_prep<DOMAIN>(sh.S, sh, tg0, tg1, tg2));
+    cand_store(cs, slot, hyp_prep<DOMAIN>(sh.S, sh, tg0, tg1, ip));    // g . (c,1) = 1 / dp
     cs.nx[slot] = (float)nx; cs.ny[slot] = (float)ny; cs.nz[slot] = (float)nz;
     cs.ig[slot] = dp;
     return true;
@@ -639,10 +697,11 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
     for (int base = 0; base < M; base += 32) {
         const int m = base + lane;
         bool ok = false;
-        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+        double g0 = 0.0, g1 = 0.0, igc = 0.0;
         if (m == 0) {
             ok = gc.w != 0.0;
-            g0 = gc.x; g1 = gc.y; g2 = gc.z;
+            g0 = gc.x; g1 = gc.y;
+            igc = gc.x * sh.cx + gc.y * sh.cy + gc.z;
         } else if (m < M) {
             int dx, dy;
             if (m <= 8) {
@@ -664,13 +723,13 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
                     const float4 pj = planes_in[j];
                     const double cosr = fabs(pj.y * sh.rx + pj.z * sh.ry + pj.w * sh.rz);
                     ok = ok && cosr >= 0.1 * sh.rn;                          // not grazing
-                    g0 = gj.x; g1 = gj.y; g2 = gj.z;
+                    g0 = gj.x; g1 = gj.y; igc = ig;
                     cs.ig[lane] = ig;
                     cs.nx[lane] = pj.y; cs.ny[lane] = pj.z; cs.nz[lane] = pj.w;
                 }
             }
         }
-        if (ok) cand_store(cs, lane, hyp_prep<DOMAIN>(S, sh, g0, g1, g2));
+        if (ok) cand_store(cs, lane, hyp_prep<DOMAIN>(S, sh, g0, g1, igc));
         cs.ec[lane] = 0.f;
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         __syncwarp();
@@ -698,11 +757,12 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
 
     // refinement step: normals of the eight ring triangles (Fig. 3b)
     int best_t = -1;
-    const double dnew = best_m > 0 ? 1.0 / sh.best_ig : (double)planes_in[gs].x;
+    const double dnew = best_m > 0 ? rcp64(sh.best_ig) : (double)planes_in[gs].x;
+    const double ignew = best_m > 0 ? sh.best_ig : rcp64(dnew);
     if (Ebest > -INFINITY && dnew > 0.0) {
         bool ok = false;
         if (lane < 8) {
-            ok = triangle_candidate<DOMAIN>(vd, dnew, lane);
+            ok = triangle_candidate<DOMAIN>(vd, dnew, ignew, lane);
         } else if (lane < 8 + vd.perturb_k) {           // flagged variant: random planes around (dnew, n)
             double n0, n1, n2;
             if (best_m > 0) {
@@ -886,12 +946,10 @@ __global__ void __launch_bounds__(128) k_score(const __grid_constant__ Workspace
     setup_sp<DOMAIN>(w, planes_state, gs, lane, S, sh, gc.w != 0.0, gc.x, gc.y, gc.z);
     __syncwarp();
     CandShared &cs = g_cs[threadIdx.x >> 5];
-    if (lane == 0) {
-        cand_store(cs, 0, hyp_prep<DOMAIN>(S, sh, g0, g1, g2));
-        cs.ec[0] = 0.f;
-    }
+    cs.ec[lane] = 0.f;
+    if (lane == 0) cand_store(cs, 0, hyp_prep<DOMAIN>(S, sh, g0, g1, g0 * sh.cx + g1 * sh.cy + g2));
     __syncwarp();
-    view_terms<DOMAIN, SLOTS_MAX, true>(w, 1u, rec);
+    view_terms<DOMAIN, SLOTS_MAX, true, true>(w, 1u, rec);
     if (lane == 0) {
         const float E = cand_energy(sh, cs, S.nnb, 0);
         rec[0] = E; rec[1] = cs.es[0]; rec[2] = S.nnb > 0 ? cs.ec[0] / (float)S.nnb : 0.f;
