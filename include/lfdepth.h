@@ -250,7 +250,9 @@ lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const 
  * D^2 = |dLab|^2 + (compactness / S)^2 |dxy|^2, S = sqrt(W H / (grid_w grid_h))
  * (ties to the first cell in row-major order), then moves each centre to the
  * mean of its pixels; a final assignment writes the labels.  No connectivity
- * post-processing.
+ * post-processing.  A pixel whose colour is not finite keeps its own cell and
+ * does not enter the means; the means take Lab values clamped to [-256, 256]
+ * (every sRGB colour in [0,1] is inside) in fixed point (2^-18). 
  *   views, view_pitch_bytes (nullable = packed), width, height, grid_w,
  *   grid_h: arrays [n] (host); images and labels_out[v] (int32 H*W) on the
  *   device.  centres_in / centres_out (nullable; entries float[grid_w*grid_h*5]

@@ -8,8 +8,8 @@
 // D^2 = |lab - lab_c|^2 + (m / S)^2 |xy - xy_c|^2, ties to the first cell in
 // row-major order; a centre becomes the mean of its pixels (kept when it has
 // none).  No connectivity post-processing: the superpixel builder accepts any
-// label map.  Deterministic: the update sums each centre's window in a fixed
-// order with a fixed reduction tree.
+// label map.  Deterministic: the update's sums are integers (Lab in fixed
+// point), so the order of their atomics does not matter.
 #include "lfd_internal.cuh"
 
 namespace lfd {
@@ -52,18 +52,10 @@ __device__ __forceinline__ void texel_rgb(int fmt, const char *row, int x, float
 }
 
 // boundary k of n cells over `size` pixels: round(k size / n), half up
+// (32-bit unsigned: 2 k size + n < 2^32 for sizes up to LFD_MAX_DIM)
 __device__ __forceinline__ int cell_edge(int k, int size, int n)
 {
-    return (int)((2LL * k * size + n) / (2LL * n));
-}
-
-// cell containing pixel coordinate p
-__device__ __forceinline__ int cell_of(int p, int size, int n)
-{
-    int k = (int)(((long long)p * n) / size);
-    while (k > 0 && cell_edge(k, size, n) > p) k--;
-    while (k < n - 1 && cell_edge(k + 1, size, n) <= p) k++;
-    return k;
+    return (int)((2u * (unsigned)k * (unsigned)size + (unsigned)n) / (2u * (unsigned)n));
 }
 
 __global__ void __launch_bounds__(256) k_slic_lab(SlicView s)
@@ -90,72 +82,129 @@ __global__ void k_slic_seeds(SlicView s)
     o[0] = l.x; o[1] = l.y; o[2] = l.z; o[3] = x; o[4] = y;
 }
 
-__global__ void __launch_bounds__(256) k_slic_assign(SlicView s, const float *centres, float wxy)
+// Fixed-point scale of the Lab sums: 2^18 (a power of two, so v * 2^18 is
+// exact and the rounding error of one value is at most 2^-19), on values
+// clamped to [-256, 256] (every sRGB colour is inside), so that a warp's sum
+// fits 32 bits.  Integer sums are associative: the update does not depend on
+// the order of the reductions and atomics.
+constexpr float SLIC_FIX = 262144.0f;
+constexpr float SLIC_LAB_MAX = 256.0f;
+
+// One CTA per grid cell (cx, cy): its pixels pick the nearest of the 3x3
+// cells' centres (ties to the first in row-major order) and, with `acc`,
+// add {L, a, b} (fixed point), x, y and 1 to the winner's sums: per warp one
+// REDUX per quantity and centre present, into the CTA's 9 bins in shared
+// memory, then 9 x 6 64-bit atomics into acc.
+constexpr int SLIC_ASSIGN_THREADS = 256;
+
+__device__ __forceinline__ int slic_fix(float v)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= s.W * s.H) return;
-    const int x = p % s.W, y = p / s.W;
-    const int cx = cell_of(x, s.W, s.GW), cy = cell_of(y, s.H, s.GH);
-    const float4 l = s.lab[p];
-    float best = INFINITY;
-    int arg = -1;
-    for (int dy = -1; dy <= 1; dy++)
-        for (int dx = -1; dx <= 1; dx++) {
-            const int nx = cx + dx, ny = cy + dy;
-            if (nx < 0 || ny < 0 || nx >= s.GW || ny >= s.GH) continue;
-            const float *c = centres + 5 * (long long)(ny * s.GW + nx);
-            const float dl = l.x - c[0], da = l.y - c[1], db = l.z - c[2];
-            const float ddx = (float)x - c[3], ddy = (float)y - c[4];
-            const float D = fmaf(dl, dl, fmaf(da, da, db * db)) + wxy * fmaf(ddx, ddx, ddy * ddy);
-            if (D < best) {
-                best = D;
-                arg = ny * s.GW + nx;
-            }
-        }
-    s.labels[p] = arg;
+    return __float2int_rn(fminf(fmaxf(v, -SLIC_LAB_MAX), SLIC_LAB_MAX) * SLIC_FIX);
 }
 
-// one warp per centre: the pixels of the 3x3 cells around its own that carry its label
-__global__ void __launch_bounds__(128) k_slic_update(SlicView s, const float *cin, float *cout)
+__global__ void __launch_bounds__(SLIC_ASSIGN_THREADS) k_slic_assign(SlicView s, const float *centres, float wxy,
+                                                                     unsigned long long *acc)
 {
-    const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
+    __shared__ float cen[9][5];
+    __shared__ int cid[9];
+    __shared__ unsigned long long bin[9][6];
     const int lane = threadIdx.x & 31;
-    if (c >= s.GW * s.GH) return;
-    const int cx = c % s.GW, cy = c / s.GW;
-    const int x0 = cell_edge(max(cx - 1, 0), s.W, s.GW), x1 = cell_edge(min(cx + 2, s.GW), s.W, s.GW);
-    const int y0 = cell_edge(max(cy - 1, 0), s.H, s.GH), y1 = cell_edge(min(cy + 2, s.GH), s.H, s.GH);
-    const int ww = x1 - x0;
-    const long long area = (long long)ww * (y1 - y0);
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
-    int n = 0;
-    for (long long i = lane; i < area; i += 32) {
-        const int x = x0 + (int)(i % ww), y = y0 + (int)(i / ww);
-        const long long p = (long long)y * s.W + x;
-        if (s.labels[p] != c) continue;
-        const float4 l = s.lab[p];
-        a0 += l.x; a1 += l.y; a2 += l.z; a3 += (float)x; a4 += (float)y;
-        n++;
+    const int cx = blockIdx.x % s.GW, cy = blockIdx.x / s.GW;
+    if (threadIdx.x < 9) {
+        const int nx = cx + threadIdx.x % 3 - 1, ny = cy + threadIdx.x / 3 - 1;
+        const bool in = nx >= 0 && ny >= 0 && nx < s.GW && ny < s.GH;
+        const int c = in ? ny * s.GW + nx : -1;
+        cid[threadIdx.x] = c;
+        for (int j = 0; j < 5; j++) cen[threadIdx.x][j] = in ? centres[5 * (long long)c + j] : 0.f;
     }
-    a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3); a4 = warp_sum(a4);
-    n = __reduce_add_sync(0xffffffffu, (unsigned)n);
-    if (lane == 0) {
-        float *o = cout + 5 * (long long)c;
-        const float *i = cin + 5 * (long long)c;
-        if (n > 0) {
-            const float r = 1.0f / (float)n;
-            o[0] = a0 * r; o[1] = a1 * r; o[2] = a2 * r; o[3] = a3 * r; o[4] = a4 * r;
-        } else {
-            for (int k = 0; k < 5; k++) o[k] = i[k];
+    if (threadIdx.x < 54) bin[threadIdx.x / 6][threadIdx.x % 6] = 0ull;
+    __syncthreads();
+    const int x0 = cell_edge(cx, s.W, s.GW), x1 = cell_edge(cx + 1, s.W, s.GW);
+    const int y0 = cell_edge(cy, s.H, s.GH), y1 = cell_edge(cy + 1, s.H, s.GH);
+    const int cw = x1 - x0, n = cw * (y1 - y0);
+    for (int base = 0; base < n; base += SLIC_ASSIGN_THREADS) {
+        if (base + (int)(threadIdx.x & ~31u) >= n) break;      // the whole warp is past the cell
+        const int i = base + threadIdx.x;
+        bool take = false;
+        int k = 4, x = 0, y = 0;
+        float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < n) {
+            y = y0 + i / cw;
+            x = x0 + i % cw;
+            const long long p = (long long)y * s.W + x;
+            l = __ldg(s.lab + p);
+            float best = INFINITY;
+            int kb = -1;
+#pragma unroll
+            for (int j = 0; j < 9; j++) {
+                if (cid[j] < 0) continue;
+                const float dl = l.x - cen[j][0], da = l.y - cen[j][1], db = l.z - cen[j][2];
+                const float ddx = (float)x - cen[j][3], ddy = (float)y - cen[j][4];
+                const float D = fmaf(dl, dl, fmaf(da, da, db * db)) + wxy * fmaf(ddx, ddx, ddy * ddy);
+                if (D < best) {
+                    best = D;
+                    kb = j;
+                }
+            }
+            take = kb >= 0;              // all distances NaN (non-finite colour): own cell, not counted
+            if (take) k = kb;
+            s.labels[p] = cid[k];
+        }
+        if (!acc) continue;
+        const int qL = take ? slic_fix(l.x) : 0, qa = take ? slic_fix(l.y) : 0, qb = take ? slic_fix(l.z) : 0;
+        unsigned present = __reduce_or_sync(0xffffffffu, take ? 1u << k : 0u);
+        while (present) {
+            const int j = __ffs(present) - 1;
+            present &= present - 1;
+            const bool me = take && k == j;
+            const int sL = __reduce_add_sync(0xffffffffu, me ? qL : 0);
+            const int sa = __reduce_add_sync(0xffffffffu, me ? qa : 0);
+            const int sb = __reduce_add_sync(0xffffffffu, me ? qb : 0);
+            const int sx = __reduce_add_sync(0xffffffffu, me ? x : 0);
+            const int sy = __reduce_add_sync(0xffffffffu, me ? y : 0);
+            const unsigned sc = __reduce_add_sync(0xffffffffu, me ? 1u : 0u);
+            if (lane == 0) {
+                atomicAdd(&bin[j][0], (unsigned long long)(long long)sL);
+                atomicAdd(&bin[j][1], (unsigned long long)(long long)sa);
+                atomicAdd(&bin[j][2], (unsigned long long)(long long)sb);
+                atomicAdd(&bin[j][3], (unsigned long long)sx);
+                atomicAdd(&bin[j][4], (unsigned long long)sy);
+                atomicAdd(&bin[j][5], (unsigned long long)sc);
+            }
         }
     }
+    if (!acc) return;
+    __syncthreads();
+    if (threadIdx.x < 54) {
+        const int j = threadIdx.x / 6, q = threadIdx.x % 6;
+        if (cid[j] >= 0 && bin[j][5]) atomicAdd(acc + 6 * (long long)cid[j] + q, bin[j][q]);
+    }
+}
+
+// centre c becomes the mean of its sums (kept when it has no pixel); the sums are cleared
+__global__ void k_slic_finalize(SlicView s, const float *cin, float *cout, unsigned long long *acc)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.GW * s.GH) return;
+    unsigned long long *a = acc + 6 * (long long)c;
+    const unsigned long long cnt = a[5];
+    float *o = cout + 5 * (long long)c;
+    if (cnt > 0) {
+        const double r = 1.0 / (double)cnt;
+        for (int j = 0; j < 3; j++) o[j] = (float)((double)(long long)a[j] * r * (1.0 / SLIC_FIX));
+        o[3] = (float)((double)a[3] * r);
+        o[4] = (float)((double)a[4] * r);
+    } else {
+        for (int j = 0; j < 5; j++) o[j] = cin[5 * (long long)c + j];
+    }
+    for (int j = 0; j < 6; j++) a[j] = 0ull;
 }
 
 cudaError_t launch_slic(const SlicView &s, const float *centres_in, int iterations, float m, float *centres_out,
                         cudaStream_t st)
 {
     const int npx = s.W * s.H, S = s.GW * s.GH;
-    const int pb = (npx + 255) / 256;
-    k_slic_lab<<<pb, 256, 0, st>>>(s);
+    k_slic_lab<<<(npx + 255) / 256, 256, 0, st>>>(s);
     float *a = s.centres, *b = s.centres2;
     if (centres_in) {
         cudaError_t e = cudaMemcpyAsync(a, centres_in, sizeof(float) * 5 * S, cudaMemcpyDeviceToDevice, st);
@@ -165,12 +214,16 @@ cudaError_t launch_slic(const SlicView &s, const float *centres_in, int iteratio
     }
     const double step = sqrt((double)npx / (double)S);
     const float wxy = (float)((m / step) * (m / step));
+    if (iterations > 0) {
+        cudaError_t e = cudaMemsetAsync(s.acc, 0, sizeof(unsigned long long) * 6 * S, st);
+        if (e != cudaSuccess) return e;
+    }
     for (int it = 0; it < iterations; it++) {
-        k_slic_assign<<<pb, 256, 0, st>>>(s, a, wxy);
-        k_slic_update<<<(S + 3) / 4, 128, 0, st>>>(s, a, b);
+        k_slic_assign<<<S, SLIC_ASSIGN_THREADS, 0, st>>>(s, a, wxy, s.acc);
+        k_slic_finalize<<<(S + 127) / 128, 128, 0, st>>>(s, a, b, s.acc);
         float *t = a; a = b; b = t;
     }
-    k_slic_assign<<<pb, 256, 0, st>>>(s, a, wxy);
+    k_slic_assign<<<S, SLIC_ASSIGN_THREADS, 0, st>>>(s, a, wxy, nullptr);
     if (centres_out) {
         cudaError_t e = cudaMemcpyAsync(centres_out, a, sizeof(float) * 5 * S, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;

@@ -352,38 +352,44 @@ cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStr
 }
 
 // ---------------------------------------------------------------------------
-// 6. work order of the propagation (and persistent sweep) launches: a stable
-//    counting sort of all superpixels by pixel-slot class (ceil(n/32), capped
-//    at 16), largest first, index order inside a class.  Superpixels of one
-//    class run the same compiled evaluation, so the warps resident on an SM at
-//    any time execute one code body (measured on the 8-view 1024x768 case:
-//    23.3 ms per frame in this order, 47 ms with the classes sorted per view,
-//    53 ms in plain index order, from instruction-fetch stalls); expensive
-//    superpixels go first.  Deterministic.
+// 6. work orders of the persistent launches: a stable counting sort of all
+//    superpixels by size class, largest first, index order inside a class.
+//    Propagation (mode 0) uses pixel-slot classes ceil(n/32), capped at 16:
+//    superpixels of one class run the same compiled evaluation, so the warps
+//    resident on an SM at any time execute one code body (measured on the
+//    8-view 1024x768 case: 23.3 ms per frame in this order, 47 ms with the
+//    classes sorted per view, 53 ms in plain index order, from
+//    instruction-fetch stalls).  The sweep (mode 1) has one code body and
+//    uses coarser power-of-two classes floor(log2 n): expensive superpixels
+//    still go first, while superpixels of similar size keep index order, so
+//    concurrently swept superpixels are neighbours and share L2 lines (slot
+//    classes there interleaved 14- and 15-pixel grid cells across all views
+//    and read 6x more DRAM).  Deterministic.
 // ---------------------------------------------------------------------------
 
 constexpr int ORDER_KEYS = 17;
 
-__device__ __forceinline__ int order_key(const Workspace &w, int gs)
+__device__ __forceinline__ int order_key(const Workspace &w, int gs, int mode)
 {
     const int n = __ldg(w.sp_cnt + gs);
-    return ORDER_KEYS - 1 - min((n + 31) >> 5, ORDER_KEYS - 1);    // 0 = largest class
+    const int cls = mode == 0 ? (n + 31) >> 5 : 31 - __clz(max(n, 1));
+    return ORDER_KEYS - 1 - min(cls, ORDER_KEYS - 1);    // 0 = largest class
 }
 
-__global__ void k_order_hist(Workspace w, int *hist)
+__global__ void k_order_hist(Workspace w, int *hist, int mode)
 {
     __shared__ int h[ORDER_KEYS];
     if (threadIdx.x < ORDER_KEYS) h[threadIdx.x] = 0;
     __syncthreads();
     const int gs = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gs < w.S_total) atomicAdd(&h[order_key(w, gs)], 1);
+    if (gs < w.S_total) atomicAdd(&h[order_key(w, gs, mode)], 1);
     __syncthreads();
     if (threadIdx.x < ORDER_KEYS && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
 }
 
 // one CTA of 1024 threads walks the superpixels in tiles of 1024; a
 // superpixel's slot is its key's start + the count of equal keys before it
-__global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *hist, int *order)
+__global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *hist, int *order, int mode)
 {
     __shared__ int run[ORDER_KEYS];                  // running position per key
     __shared__ int wcnt[32][ORDER_KEYS];             // per-warp counts of the tile
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *
         __syncthreads();
         const int gs = base + t;
         const bool in = gs < w.S_total;
-        const int key = in ? order_key(w, gs) : ORDER_KEYS;          // out-of-range lanes use a key of their own
+        const int key = in ? order_key(w, gs, mode) : ORDER_KEYS;    // out-of-range lanes use a key of their own
         const unsigned same = __match_any_sync(0xffffffffu, key);
         const int rank = __popc(same & ((1u << lane) - 1u));
         if (in && rank == 0) wcnt[wid][key] = __popc(same);
@@ -420,13 +426,13 @@ __global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *
     }
 }
 
-cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, cudaStream_t st)
+cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * ORDER_KEYS, st);
     if (e != cudaSuccess) return e;
     const int blocks = (w.S_total + 255) / 256;
-    k_order_hist<<<blocks, 256, 0, st>>>(w, hist);
-    k_order_scatter<<<1, 1024, 0, st>>>(w, hist, order);
+    k_order_hist<<<blocks, 256, 0, st>>>(w, hist, mode);
+    k_order_scatter<<<1, 1024, 0, st>>>(w, hist, order, mode);
     return cudaGetLastError();
 }
 

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(THREADS) k_sweep(Workspace w, Consts c, float4
     sweep_sp<FMT, WORLD, THREADS>(w, c, blockIdx.x, sh, planes, label_out, cost_out);
 }
 
-// persistent CTAs: superpixels taken from the cost-ordered queue, most expensive first
+// persistent CTAs: superpixels taken from the size-ordered queue, largest class first
 template <int FMT, bool WORLD, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_sweep_persistent(Workspace w, Consts c, float4 *planes, int *label_out,
                                                               float *cost_out)
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(THREADS) k_sweep_persistent(Workspace w, Const
         const int item = sh.item;
         __syncthreads();
         if (item >= w.S_total) break;
-        sweep_sp<FMT, WORLD, THREADS>(w, c, __ldg(w.order + item), sh, planes, label_out, cost_out);
+        sweep_sp<FMT, WORLD, THREADS>(w, c, __ldg(w.order_sweep + item), sh, planes, label_out, cost_out);
         __syncthreads();
     }
 }

@@ -199,7 +199,7 @@ struct lfd_ctx {
     short *d_radii = nullptr;
     int *d_radii_cnt = nullptr;
     DevCounters *d_ctr = nullptr;
-    int *d_order = nullptr, *d_hist = nullptr, *d_queue = nullptr;
+    int *d_order = nullptr, *d_order_sweep = nullptr, *d_hist = nullptr, *d_queue = nullptr;
     float **d_depth_ptrs = nullptr;
     float4 *d_planesA = nullptr, *d_planesB = nullptr;
     int *d_label = nullptr, *d_choice = nullptr;
@@ -407,9 +407,9 @@ cudaEvent_t prof_event(lfd_ctx *ctx)
 
 // Runs `launch` (returns cudaError_t) bracketed by events when tracing.
 template <typename F>
-cudaError_t traced(lfd_ctx *ctx, int stage, cudaStream_t st, F launch)
+cudaError_t traced(lfd_ctx *ctx, int stage, cudaStream_t st, F launch, int kernels = 1)
 {
-    ctx->launches[stage]++;
+    ctx->launches[stage] += kernels;    // kernels the launch function enqueues
     if (!ctx->prof) return launch();
     cudaEvent_t a = prof_event(ctx), b = prof_event(ctx);
     if (!a || !b) return launch();
@@ -463,7 +463,7 @@ size_t workspace_need(const Layout &L, int fmt)
     add(4 * S); add(4 * (S + 1)); add(4 * S); add(4 * P);
     add(8 * S); add(16 * S); add(16 * S); add(32 * S); add(16 * S); add(16 * S);
     add(sizeof(DevCounters));
-    add(4 * S); add(4 * ORDER_KEYS_HOST); add(16); add(sizeof(float *) * V);
+    add(4 * S); add(4 * S); add(4 * ORDER_KEYS_HOST); add(16); add(sizeof(float *) * V);
     add(16 * S); add(16 * S); add(4 * S); add(8 * S); add(8 * S);
     for (int v = 0; v < V; v++) add((size_t)qb * L.W[v] * L.H[v]);
     for (int v = 0; v < V; v++) add((size_t)16 * L.W[v] * L.H[v]);
@@ -522,6 +522,7 @@ lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
     ctx->d_bbox = (int4 *)a.take(16 * S);
     ctx->d_ctr = (DevCounters *)a.take(sizeof(DevCounters));
     ctx->d_order = (int *)a.take(4 * S);
+    ctx->d_order_sweep = (int *)a.take(4 * S);
     ctx->d_hist = (int *)a.take(4 * ORDER_KEYS_HOST);
     ctx->d_queue = (int *)a.take(16);
     ctx->d_depth_ptrs = (float **)a.take(sizeof(float *) * V);
@@ -551,6 +552,7 @@ lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
     w.radii_cnt = ctx->d_radii_cnt;
     w.ctr = ctx->d_ctr;
     w.order = ctx->d_order;
+    w.order_sweep = ctx->d_order_sweep;
     w.queue = ctx->d_queue;
     w.S_total = L.S_total;
     w.px_total = L.px_total;
@@ -706,7 +708,7 @@ lfd_status enqueue_input(lfd_ctx *ctx, cudaStream_t st, bool record_event)
     }
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
         return launch_sp_count(ctx->w, V, L.max_px, ctx->d_sp_cnt, ctx->d_bbox, st);
-    }));
+    }, 2));
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st,
                     [&] { return launch_sp_scan(ctx->w, V, ctx->d_sp_cnt, ctx->d_sp_off, st); }));
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
@@ -715,9 +717,12 @@ lfd_status enqueue_input(lfd_ctx *ctx, cudaStream_t st, bool record_event)
     }));
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_sp_minw(ctx->w, ctx->c, ctx->d_sp_col, st); }));
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_quads(ctx->w, V, L.max_px, ctx->fmt, st); }));
-    // work order of the propagation kernels: by descending size class, index order inside
+    // work orders: propagation by descending slot class, the sweep by descending
+    // power-of-two size class, index order inside a class
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st,
-                    [&] { return launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, st); }));
+                    [&] { return launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, 0, st); }, 2));
+    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st,
+                    [&] { return launch_sp_order(ctx->w, ctx->d_order_sweep, ctx->d_hist, 1, st); }, 2));
     return LFD_OK;
 }
 
@@ -1493,7 +1498,7 @@ lfd_status lfd_fuse(lfd_ctx *ctx, const float *const *depth_in, float *const *de
         a.depth_out = (float *const *)(d + o_out);
         a.mats = (const float *)(d + o_mats);
         a.zbuf = ctx->d_zbuf;
-        LFD_CUDA(traced(ctx, LFD_STAGE_FUSION, st, [&] { return launch_fuse(a, zw, max_px, st); }));
+        LFD_CUDA(traced(ctx, LFD_STAGE_FUSION, st, [&] { return launch_fuse(a, zw, max_px, st); }, 3));
     }
     return LFD_OK;
 }
@@ -1521,7 +1526,8 @@ lfd_status lfd_slic(lfd_ctx *ctx, int32_t n, const void *const *views, const int
         const long long pitch = view_pitch_bytes && view_pitch_bytes[v] ? view_pitch_bytes[v] : (long long)width[v] * tb;
         if (pitch < (long long)width[v] * tb || pitch % tb)
             return fail(ctx, LFD_ERR_INVALID_ARG, "lfd_slic: view %d: bad pitch", v);
-        const size_t b = align_up(16 * (size_t)width[v] * height[v], 256) + 2 * align_up(20 * (size_t)grid_w[v] * grid_h[v], 256);
+        const size_t b = align_up(16 * (size_t)width[v] * height[v], 256) + 2 * align_up(20 * (size_t)grid_w[v] * grid_h[v], 256) +
+                         48 * (size_t)grid_w[v] * grid_h[v];
         need = std::max(need, b);
     }
     if ((s = ensure_dev(ctx, &ctx->d_slic, &ctx->slic_cap, need)) != LFD_OK) return s;
@@ -1541,6 +1547,7 @@ lfd_status lfd_slic(lfd_ctx *ctx, int32_t n, const void *const *views, const int
         sv.lab = (float4 *)base;
         sv.centres = (float *)(base + o_c);
         sv.centres2 = (float *)(base + o_c + sz_c);
+        sv.acc = (unsigned long long *)(base + o_c + 2 * sz_c);
         sv.labels = labels_out[v];
         LFD_CUDA(launch_slic(sv, centres_in ? centres_in[v] : nullptr, iterations, (float)compactness,
                              centres_out ? centres_out[v] : nullptr, st));

@@ -108,6 +108,7 @@ struct Workspace {
     const int *radii_cnt;    // [V][LFD_MAX_ITER_INDEX + 1]
     DevCounters *ctr;
     const int *order;        // [S_total] work order: descending pixel-slot class, index order inside
+    const int *order_sweep;  // [S_total] sweep work order: descending power-of-two size class, index order inside
     int *queue;              // [4] work-queue counters of persistent launches
     int S_total;
     long long px_total;
@@ -133,6 +134,7 @@ struct SlicView {
     float4 *lab;                     // [W*H] CIELAB of the view (scratch)
     int *labels;                     // [W*H] output
     float *centres, *centres2;       // [GW*GH][5] {L, a, b, x, y} (scratch, ping-pong)
+    unsigned long long *acc;         // [GW*GH][6] update sums {L, a, b (fixed point), x, y, count} (scratch)
 };
 
 // ---------------------------------------------------------------------------
@@ -225,7 +227,8 @@ cudaError_t launch_sp_collect(const Workspace &w, const Consts &c, const int4 *b
                               double2 *cen, int2 *ref, float4 *col, cudaStream_t st);
 cudaError_t launch_sp_minw(const Workspace &w, const Consts &c, float4 *col, cudaStream_t st);
 cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStream_t st);
-cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, cudaStream_t st);  // hist: 17 ints
+// mode 0: pixel-slot classes ceil(n/32) (propagation); mode 1: power-of-two classes floor(log2 n) (sweep)
+cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, cudaStream_t st);  // hist: 17 ints
 cudaError_t launch_sweep(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
                          float *cost, cudaStream_t st);
 cudaError_t launch_plane_prep(const Workspace &w, const Consts &c, const float4 *planes, double4_32a *g, float4 *rc,
