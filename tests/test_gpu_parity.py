@@ -420,3 +420,43 @@ def test_invalid_inputs_are_reported(lfd, cfg1):
     assert e.value.status == 6 and "view 1" in str(e.value)
     ctx.set_input(views, labels, lf.rig.K, lf.rig.R, lf.rig.t, lf.GW, lf.GH, params)
     ctx.synchronize()                                # status cleared, context usable
+
+
+# ---------------------------------------------------------------------------
+# superpixel sizes across the compiled slot classes: small (1-2 slots per lane),
+# the largest staged class (10 slots) and superpixels beyond the staged 320
+# pixels (streamed), on config 1's views with other grid pitches
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("pitch", [5.0, 24.0, 40.0])
+def test_sweep_and_iterations_across_superpixel_sizes(lfd, pitch):
+    import dataclasses
+    base = synth.make_config(1)
+    W, H = base.rig.W, base.rig.H
+    labs = []
+    for v in range(base.rig.V):
+        lab, GW, GH = synth.grid_labels(W, H, pitch, True, seed=1000 + v)
+        labs.append(lab)
+    lf = dataclasses.replace(base, labels=np.stack(labs), GW=GW, GH=GH, pitch=pitch)
+    views, labels, rgb = PT.gpu_inputs(lf, "rgba8")
+    params = synth.method_params(lf, iterations=2)
+    o = PT.make_oracle(lf, rgb, params)
+    sizes = np.array([o.sp_stats(v)["cnt"] for v in range(lf.rig.V)]).ravel()
+    rep = {}
+    ok, same, adm, ne = _sweep_compare(lfd, lf, views, labels, params, o, rep)
+    print(f"\npitch {pitch}: superpixel sizes {sizes.min()}..{sizes.max()}, sweep:", rep)
+    assert ok.all() and adm[ne].all() and rep["identical_when_decided"] == 1.0
+    ctx = bind(lfd, lf, views, labels, params)
+    planes, _, _ = ctx.plane_sweep()
+    state = planes.cpu().numpy()
+    items = np.arange(o.S_total, dtype=np.int32)
+    for it in (1, 2):
+        rep = {}
+        out, same, adm = _iterate_compare(lfd, ctx, o, state, it, items, rep)
+        print(f"pitch {pitch} iteration {it} state-injected:", rep)
+        assert adm.all() and rep["identical_when_decided"] == 1.0
+        state = out
+    if pitch >= 24.0:
+        assert sizes.max() > 320          # the streamed path ran
+    else:
+        assert sizes.max() <= 64          # one- and two-slot classes
