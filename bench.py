@@ -122,6 +122,20 @@ def workload_name(cfg: int, lf) -> str:
             f"{p['num_labels']} labels, {p['iterations']} iterations")
 
 
+def replica_reduce(ms: float, units: float, ws: int, device) -> tuple[float, float]:
+    """Replicas (one process per GPU, no data exchange between them): the step
+    time is the slowest rank's and the throughput is the units all ranks
+    processed over that time.  Returns (max ms over ranks, units per second)."""
+    if ws > 1:
+        import torch.distributed as dist
+        mx = torch.tensor([ms], dtype=torch.float64, device=device)
+        sm = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms, units = float(mx.item()), float(sm.item())
+    return ms, units / (ms / 1000.0)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -334,13 +348,9 @@ def run_ours(args):
     prof = ctx.profile_read()
     ctx.profile_enable(False)
     ctx.synchronize()
-    ms = float(np.mean(step_ms))
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = hyp_step * ws / (ms / 1000.0)
+    ms_local = float(np.mean(step_ms))
+    ms, value = replica_reduce(ms_local, hyp_step, ws, dev)
+    _, samples_per_s = replica_reduce(ms_local, samples_step, ws, dev)
 
     # dominant kernel and its roofline
     stage_ms = {k: v[0] / args.steps for k, v in prof.items()}
@@ -371,7 +381,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(args.config, lf), "l2": "flushed between steps (256 MiB write)",
                        "inputs": "device-resident", "parallelism": f"replicas x{ws}"},
-            "ms_per_view": ms / V, "samples_per_s": samples_step * ws / (ms / 1000.0),
+            "ms_per_view": ms / V, "samples_per_s": samples_per_s,
             "hypotheses_per_step": hyp_step, "samples_per_step": samples_step,
             "stage_ms": stage_ms, "wall_s": wall,
             "gpu_launches": int(sum(v[1] for v in prof.values())),
@@ -428,13 +438,8 @@ def run_ours(args):
             ctx_h.estimate_host(vh, lh, K, R, t, GW, GH, params, ph, dh)
             evs[k][1].record(stream)
         barrier()
-        e_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
-        if ws > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
-        line["e2e"] = {"value": hyp_step * ws / (e_ms / 1000.0), "unit": UNIT,
+        e_ms, e_value = replica_reduce(float(np.mean([a.elapsed_time(b) for a, b in evs])), hyp_step, ws, dev)
+        line["e2e"] = {"value": e_value, "unit": UNIT,
                        "h2d_bytes_per_step": int(vh.numel() * vh.element_size() + lh.numel() * 4),
                        "d2h_bytes_per_step": int(ph.numel() * 4 + dh.numel() * 4), "ms_per_step": e_ms}
         ctx_h.close()
@@ -512,14 +517,11 @@ def run_ours_batch(args):
         ev[k][1].record(stream)
     barrier()
     clock_info = clocks.stop()
-    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ms_local = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     prof = ctx.profile_read()
     ctx.profile_enable(False)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms, value = replica_reduce(ms_local, hyp_step, ws, dev)
+    _, samples_per_s = replica_reduce(ms_local, samples_step, ws, dev)
     stage_ms = {k: v[0] / args.steps for k, v in prof.items()}
     stage_launches = {k: v[1] / args.steps for k, v in prof.items()}
     sweep_samples = sum(int(m.params["num_labels"]) * m.rig.V * m.rig.W * m.rig.H * min(m.rig.V - 1, 8)
@@ -541,14 +543,14 @@ def run_ours_batch(args):
                 "algorithmic": f"{FLOPS_PER_SAMPLE[dom]} FP32 flop per pixel-view sample x "
                                f"{dom_samples / launches:.4g} samples per launch",
                 "avg_launch_ms": avg_launch_ms}
-    line = {"metric": METRIC, "value": hyp_step * ws / (ms / 1000.0), "unit": UNIT, "n_gpus": ws,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": mix_workload_name(len(mix), args.scale),
                        "superpixels": int(sum(m.rig.V * m.GW * m.GH for m in mix)),
                        "l2": "flushed between steps (256 MiB write)",
                        "inputs": "device-resident", "parallelism": f"replicas x{ws}"},
-            "samples_per_s": samples_step * ws / (ms / 1000.0), "hypotheses_per_step": hyp_step,
+            "samples_per_s": samples_per_s, "hypotheses_per_step": hyp_step,
             "samples_per_step": samples_step, "stage_ms": stage_ms,
             "gpu_launches": int(sum(v[1] for v in prof.values())), "launch_config": ctx.launch_config(),
             "roofline": roofline, "clocks": clock_info, "input_generation_s": t_gen}
@@ -578,8 +580,8 @@ def run_ours_batch(args):
             e2e_step()
             evs[k][1].record(stream)
         barrier()
-        e_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
-        line["e2e"] = {"value": hyp_step * ws / (e_ms / 1000.0), "unit": UNIT,
+        e_ms, e_value = replica_reduce(float(np.mean([a.elapsed_time(b) for a, b in evs])), hyp_step, ws, dev)
+        line["e2e"] = {"value": e_value, "unit": UNIT,
                        "h2d_bytes_per_step": int(sum(a.numel() for a in vh) + 4 * sum(b.numel() for b in lh)),
                        "d2h_bytes_per_step": int(4 * ph.numel() + 4 * sum(a.numel() for a in dh)),
                        "ms_per_step": e_ms}
