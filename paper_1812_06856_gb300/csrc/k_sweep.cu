@@ -121,8 +121,12 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
         const bool active = k < L;
         const double u = vd.jitter ? jitter_u(vd.seed, vd.lf_index, vd.lv, s, active ? k : 0) : 0.5;
         const double z = vd.inv_dmax + ((double)(active ? k : 0) + u) * vd.delta;
-        float cost = 0.f;
+        // the label's cost is summed per chunk (at most 128 pixels times the
+        // neighbour views) and the chunk sums are added up, which keeps the
+        // FP32 sum within ~1e-5 relative for superpixels of any size
+        float total = 0.f;
         for (int pc = 0; pc < n; pc += SWEEP_CHUNK) {
+            float cost = 0.f;
             const int cn = min(SWEEP_CHUNK, n - pc);
             __syncthreads();
             for (int i = threadIdx.x; i < cn; i += THREADS) {
@@ -183,7 +187,9 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
                     }
                 }
             }
+            total += cost;
         }
+        const float cost = total;
         if (active) {
             if (cost_out) cost_out[(long long)gs * c.L + k] = cost * c.col_scale * c.col_scale;
             if (cost < best_cost) {   // k increases within a thread: strict < keeps the lowest k

@@ -95,7 +95,7 @@ def _sweep_compare(lfd, lf, views, labels, params, o, report):
     # than the tolerance; there the GPU must agree exactly
     decided = np.array([ne[i] and PT.separated_best(-sw["cost"][i], -sw["cost_hi"][i], -sw["cost_lo"][i], sw["label"][i])
                         for i in range(len(lab))])
-    report.update(cost_ok=float(ok.mean()), cost_max_rel_err_unflagged=float(err.max()),
+    report.update(cost_ok=float(ok.mean()), cost_max_rel_err_unflagged=float(err.max()) if err.size else 0.0,
                   cost_flagged=float(1 - unfl.mean()), label_identical=float(same[ne].mean()),
                   label_admissible=float(adm[ne].mean()), decided=float(decided[ne].mean()),
                   identical_when_decided=float(same[decided].mean()) if decided.any() else 1.0)
