@@ -36,8 +36,11 @@ import torch  # noqa: E402
 METRIC = "plane-hypothesis evals/s"
 UNIT = "evals/s"
 L2_FLUSH_BYTES = 256 << 20
-# algorithmic FP32 operations per pixel-view sample (counted from the method's
-# arithmetic, address arithmetic excluded)
+# algorithmic FP32 operations per pixel-view sample, counted from the method's
+# arithmetic (address arithmetic excluded): sweep = projection 15, floor and
+# fraction 2, bilinear 19, SSD 8, truncation and accumulation 2; propagation =
+# projection 12, reciprocal 1, division 2, rounding 2, Eq. 9 weight 8, X/Y
+# test 2, Eq. 10 Gaussian 4, accumulation 4
 FLOPS_PER_SAMPLE = {"sweep": 46, "propagate": 35}
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128

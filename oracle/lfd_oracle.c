@@ -1143,7 +1143,7 @@ void orc_iterate(void *h, int32_t iter, const double *planes_in, const int32_t *
 }
 
 /* Refinement candidates of one superpixel for a given post-propagation depth
- * (used to judge a divergent propagation choice).  out: 8*3 (E, lo, hi). */
+ * (used to assess a divergent propagation choice).  out: 8*3 (E, lo, hi). */
 int32_t orc_refine_candidates(void *h, const double *planes_state, int32_t gsp, double dnew, double nx, double ny,
                               double nz, int32_t iter, double *out)
 {

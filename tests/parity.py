@@ -20,7 +20,7 @@ import torch
 from oracle import oracle as orc
 from paper_1812_06856_gb300 import synth
 
-REL = 1e-4      # the benchmark spec per-hypothesis tolerance
+REL = 1e-4      # per-hypothesis relative tolerance of the path's floating-point terms
 ABS = 1e-6      # absolute floor for terms of O(1) magnitude computed with FP32 exp/rcp
 TIE_REL = 2.5e-4
 
