@@ -293,7 +293,8 @@ def run_reference(args):
             "config": {"workload": mix_workload_name(args.mix, args.scale) if args.config == 4
                        else workload_name(args.config, lf), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0, "roofline": None, "clocks": None}     # host cores only
     print(json.dumps(line), flush=True)
 
 
