@@ -9,7 +9,8 @@
 // row-major order; a centre becomes the mean of its pixels (kept when it has
 // none).  No connectivity post-processing: the superpixel builder accepts any
 // label map.  Deterministic: the update's sums are integers (Lab in fixed
-// point), so the order of their atomics does not matter.
+// point), so the order of their atomics does not matter.  Up to SLIC_BATCH
+// views go through the same launches (blockIdx.y = view).
 #include "lfd_internal.cuh"
 
 namespace lfd {
@@ -58,8 +59,9 @@ __device__ __forceinline__ int cell_edge(int k, int size, int n)
     return (int)((2u * (unsigned)k * (unsigned)size + (unsigned)n) / (2u * (unsigned)n));
 }
 
-__global__ void __launch_bounds__(256) k_slic_lab(SlicView s)
+__global__ void __launch_bounds__(256) k_slic_lab(const __grid_constant__ SlicBatch bt)
 {
+    const SlicView &s = bt.v[blockIdx.y];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= s.W * s.H) return;
     const int x = p % s.W, y = p / s.W;
@@ -69,8 +71,9 @@ __global__ void __launch_bounds__(256) k_slic_lab(SlicView s)
     s.lab[p] = make_float4(l.x, l.y, l.z, 0.f);
 }
 
-__global__ void k_slic_seeds(SlicView s)
+__global__ void k_slic_seeds(const __grid_constant__ SlicBatch b)
 {
+    const SlicView &s = b.v[blockIdx.y];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= s.GW * s.GH) return;
     const int cx = c % s.GW, cy = c / s.GW;
@@ -102,9 +105,14 @@ __device__ __forceinline__ int slic_fix(float v)
     return __float2int_rn(fminf(fmaxf(v, -SLIC_LAB_MAX), SLIC_LAB_MAX) * SLIC_FIX);
 }
 
-__global__ void __launch_bounds__(SLIC_ASSIGN_THREADS) k_slic_assign(SlicView s, const float *centres, float wxy,
-                                                                     unsigned long long *acc)
+__global__ void __launch_bounds__(SLIC_ASSIGN_THREADS) k_slic_assign(const __grid_constant__ SlicBatch b, int parity,
+                                                                     bool accumulate)
 {
+    const SlicView &s = b.v[blockIdx.y];
+    if ((int)blockIdx.x >= s.GW * s.GH) return;                // past this view's cells (whole CTA)
+    const float *centres = parity ? s.centres2 : s.centres;
+    unsigned long long *acc = accumulate ? s.acc : nullptr;
+    const float wxy = b.wxy[blockIdx.y];
     __shared__ float cen[9][5];
     __shared__ int cid[9];
     __shared__ unsigned long long bin[9][6];
@@ -182,10 +190,14 @@ __global__ void __launch_bounds__(SLIC_ASSIGN_THREADS) k_slic_assign(SlicView s,
 }
 
 // centre c becomes the mean of its sums (kept when it has no pixel); the sums are cleared
-__global__ void k_slic_finalize(SlicView s, const float *cin, float *cout, unsigned long long *acc)
+__global__ void k_slic_finalize(const __grid_constant__ SlicBatch b, int parity)
 {
+    const SlicView &s = b.v[blockIdx.y];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= s.GW * s.GH) return;
+    const float *cin = parity ? s.centres2 : s.centres;
+    float *cout = parity ? s.centres : s.centres2;
+    unsigned long long *acc = s.acc;
     unsigned long long *a = acc + 6 * (long long)c;
     const unsigned long long cnt = a[5];
     float *o = cout + 5 * (long long)c;
@@ -200,32 +212,43 @@ __global__ void k_slic_finalize(SlicView s, const float *cin, float *cout, unsig
     for (int j = 0; j < 6; j++) a[j] = 0ull;
 }
 
-cudaError_t launch_slic(const SlicView &s, const float *centres_in, int iterations, float m, float *centres_out,
-                        cudaStream_t st)
+cudaError_t launch_slic(const SlicBatch &b, const float *const *centres_in, int iterations,
+                        float *const *centres_out, cudaStream_t st)
 {
-    const int npx = s.W * s.H, S = s.GW * s.GH;
-    k_slic_lab<<<(npx + 255) / 256, 256, 0, st>>>(s);
-    float *a = s.centres, *b = s.centres2;
-    if (centres_in) {
-        cudaError_t e = cudaMemcpyAsync(a, centres_in, sizeof(float) * 5 * S, cudaMemcpyDeviceToDevice, st);
+    const dim3 g_px((b.max_px + 255) / 256, b.n), g_cells((b.max_cells + 127) / 128, b.n), g_cta(b.max_cells, b.n);
+    k_slic_lab<<<g_px, 256, 0, st>>>(b);
+    bool seeds = false;
+    for (int v = 0; v < b.n; v++) {
+        const SlicView &s = b.v[v];
+        const size_t S = (size_t)s.GW * s.GH;
+        cudaError_t e = cudaSuccess;
+        if (centres_in && centres_in[v])
+            e = cudaMemcpyAsync(s.centres, centres_in[v], sizeof(float) * 5 * S, cudaMemcpyDeviceToDevice, st);
+        else
+            seeds = true;
+        if (e == cudaSuccess && iterations > 0) e = cudaMemsetAsync(s.acc, 0, sizeof(unsigned long long) * 6 * S, st);
         if (e != cudaSuccess) return e;
-    } else {
-        k_slic_seeds<<<(S + 127) / 128, 128, 0, st>>>(s);
     }
-    const double step = sqrt((double)npx / (double)S);
-    const float wxy = (float)((m / step) * (m / step));
-    if (iterations > 0) {
-        cudaError_t e = cudaMemsetAsync(s.acc, 0, sizeof(unsigned long long) * 6 * S, st);
-        if (e != cudaSuccess) return e;
+    if (seeds) {
+        // views with given centres keep them: seed only the others
+        SlicBatch bs = b;
+        int k = 0;
+        for (int v = 0; v < b.n; v++)
+            if (!(centres_in && centres_in[v])) bs.v[k++] = b.v[v];
+        bs.n = k;
+        k_slic_seeds<<<dim3((b.max_cells + 127) / 128, k), 128, 0, st>>>(bs);
     }
     for (int it = 0; it < iterations; it++) {
-        k_slic_assign<<<S, SLIC_ASSIGN_THREADS, 0, st>>>(s, a, wxy, s.acc);
-        k_slic_finalize<<<(S + 127) / 128, 128, 0, st>>>(s, a, b, s.acc);
-        float *t = a; a = b; b = t;
+        k_slic_assign<<<g_cta, SLIC_ASSIGN_THREADS, 0, st>>>(b, it & 1, true);
+        k_slic_finalize<<<g_cells, 128, 0, st>>>(b, it & 1);
     }
-    k_slic_assign<<<S, SLIC_ASSIGN_THREADS, 0, st>>>(s, a, wxy, nullptr);
-    if (centres_out) {
-        cudaError_t e = cudaMemcpyAsync(centres_out, a, sizeof(float) * 5 * S, cudaMemcpyDeviceToDevice, st);
+    const int parity = iterations & 1;
+    k_slic_assign<<<g_cta, SLIC_ASSIGN_THREADS, 0, st>>>(b, parity, false);
+    for (int v = 0; v < b.n && centres_out; v++) {
+        if (!centres_out[v]) continue;
+        const SlicView &s = b.v[v];
+        cudaError_t e = cudaMemcpyAsync(centres_out[v], parity ? s.centres2 : s.centres,
+                                        sizeof(float) * 5 * (size_t)s.GW * s.GH, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();

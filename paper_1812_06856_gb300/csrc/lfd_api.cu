@@ -1518,7 +1518,11 @@ lfd_status lfd_slic(lfd_ctx *ctx, int32_t n, const void *const *views, const int
         return fail(ctx, LFD_ERR_INVALID_ARG, "lfd_slic: bad arguments");
     if (!(compactness > 0.0) || iterations < 0 || iterations > 1000)
         return fail(ctx, LFD_ERR_INVALID_ARG, "compactness must be > 0 and iterations 0..1000");
-    size_t need = 0;
+    auto view_bytes = [&](int v, size_t &o_c, size_t &sz_c) {
+        o_c = align_up(16 * (size_t)width[v] * height[v], 256);
+        sz_c = align_up(20 * (size_t)grid_w[v] * grid_h[v], 256);
+        return o_c + 2 * sz_c + align_up(48 * (size_t)grid_w[v] * grid_h[v], 256);
+    };
     for (int v = 0; v < n; v++) {
         if (width[v] < 1 || height[v] < 1 || width[v] > LFD_MAX_DIM || height[v] > LFD_MAX_DIM || grid_w[v] < 1 ||
             grid_h[v] < 1 || grid_w[v] > width[v] || grid_h[v] > height[v] || !views[v] || !labels_out[v])
@@ -1526,31 +1530,46 @@ lfd_status lfd_slic(lfd_ctx *ctx, int32_t n, const void *const *views, const int
         const long long pitch = view_pitch_bytes && view_pitch_bytes[v] ? view_pitch_bytes[v] : (long long)width[v] * tb;
         if (pitch < (long long)width[v] * tb || pitch % tb)
             return fail(ctx, LFD_ERR_INVALID_ARG, "lfd_slic: view %d: bad pitch", v);
-        const size_t b = align_up(16 * (size_t)width[v] * height[v], 256) + 2 * align_up(20 * (size_t)grid_w[v] * grid_h[v], 256) +
-                         48 * (size_t)grid_w[v] * grid_h[v];
-        need = std::max(need, b);
+    }
+    // scratch for one group of up to SLIC_BATCH views at a time
+    size_t need = 0;
+    for (int g = 0; g < n; g += SLIC_BATCH) {
+        size_t sum = 0, o_c, sz_c;
+        for (int v = g; v < std::min(n, g + SLIC_BATCH); v++) sum += view_bytes(v, o_c, sz_c);
+        need = std::max(need, sum);
     }
     if ((s = ensure_dev(ctx, &ctx->d_slic, &ctx->slic_cap, need)) != LFD_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    for (int v = 0; v < n; v++) {
-        SlicView sv;
-        sv.W = width[v];
-        sv.H = height[v];
-        sv.GW = grid_w[v];
-        sv.GH = grid_h[v];
-        sv.fmt = fmt;
-        sv.pad = 0;
-        sv.pitch = view_pitch_bytes && view_pitch_bytes[v] ? view_pitch_bytes[v] : (long long)width[v] * tb;
-        sv.img = views[v];
+    for (int g = 0; g < n; g += SLIC_BATCH) {
+        SlicBatch b = {};
+        b.n = std::min(n - g, SLIC_BATCH);
         char *base = (char *)ctx->d_slic;
-        const size_t o_c = align_up(16 * (size_t)sv.W * sv.H, 256), sz_c = align_up(20 * (size_t)sv.GW * sv.GH, 256);
-        sv.lab = (float4 *)base;
-        sv.centres = (float *)(base + o_c);
-        sv.centres2 = (float *)(base + o_c + sz_c);
-        sv.acc = (unsigned long long *)(base + o_c + 2 * sz_c);
-        sv.labels = labels_out[v];
-        LFD_CUDA(launch_slic(sv, centres_in ? centres_in[v] : nullptr, iterations, (float)compactness,
-                             centres_out ? centres_out[v] : nullptr, st));
+        for (int k = 0; k < b.n; k++) {
+            const int v = g + k;
+            SlicView &sv = b.v[k];
+            size_t o_c, sz_c;
+            const size_t bytes = view_bytes(v, o_c, sz_c);
+            sv.W = width[v];
+            sv.H = height[v];
+            sv.GW = grid_w[v];
+            sv.GH = grid_h[v];
+            sv.fmt = fmt;
+            sv.pad = 0;
+            sv.pitch = view_pitch_bytes && view_pitch_bytes[v] ? view_pitch_bytes[v] : (long long)width[v] * tb;
+            sv.img = views[v];
+            sv.lab = (float4 *)base;
+            sv.centres = (float *)(base + o_c);
+            sv.centres2 = (float *)(base + o_c + sz_c);
+            sv.acc = (unsigned long long *)(base + o_c + 2 * sz_c);
+            sv.labels = labels_out[v];
+            base += bytes;
+            const double step = std::sqrt((double)sv.W * sv.H / ((double)sv.GW * sv.GH));
+            b.wxy[k] = (float)((compactness / step) * (compactness / step));
+            b.max_px = std::max(b.max_px, sv.W * sv.H);
+            b.max_cells = std::max(b.max_cells, sv.GW * sv.GH);
+        }
+        LFD_CUDA(launch_slic(b, centres_in ? centres_in + g : nullptr, iterations, centres_out ? centres_out + g : nullptr,
+                             st));
     }
     return LFD_OK;
 }
