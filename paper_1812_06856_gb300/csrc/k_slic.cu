@@ -11,7 +11,7 @@
 // label map.  Deterministic: the update's sums are integers (Lab in fixed
 // point), so the order of their atomics does not matter.  Up to SLIC_BATCH
 // views go through the same launches (blockIdx.y = view).
-#include "lfd_internal.cuh"
+#include "lfd_slic.cuh"
 
 namespace lfd {
 

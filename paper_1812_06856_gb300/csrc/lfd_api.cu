@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "lfd_internal.cuh"
+#include "lfd_slic.cuh"
 
 using namespace lfd;
 

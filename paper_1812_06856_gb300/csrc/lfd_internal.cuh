@@ -126,25 +126,6 @@ struct FuseArgs {
     unsigned *zbuf;
 };
 
-// one view of a SLIC segmentation
-struct SlicView {
-    int W, H, GW, GH, fmt, pad;
-    long long pitch;                 // bytes per image row
-    const void *img;
-    float4 *lab;                     // [W*H] CIELAB of the view (scratch)
-    int *labels;                     // [W*H] output
-    float *centres, *centres2;       // [GW*GH][5] {L, a, b, x, y} (scratch, ping-pong)
-    unsigned long long *acc;         // [GW*GH][6] update sums {L, a, b (fixed point), x, y, count} (scratch)
-};
-
-// up to SLIC_BATCH views segmented by the same launches (blockIdx.y = view)
-constexpr int SLIC_BATCH = 16;
-struct SlicBatch {
-    SlicView v[SLIC_BATCH];
-    float wxy[SLIC_BATCH];                // (m / S)^2 of each view
-    int n, max_px, max_cells, pad;
-};
-
 // ---------------------------------------------------------------------------
 // small device helpers
 // ---------------------------------------------------------------------------
@@ -246,8 +227,6 @@ cudaError_t launch_propagate(const Workspace &w, const Consts &c, const LaunchCf
                              const float4 *planes_in, float4 *planes_out, int *choice, float *energy,
                              cudaStream_t st);
 cudaError_t launch_fuse(const FuseArgs &a, long long zbuf_words, int max_px, cudaStream_t st);
-cudaError_t launch_slic(const SlicBatch &b, const float *const *centres_in, int iterations,
-                        float *const *centres_out, cudaStream_t st);
 cudaError_t launch_score(const Workspace &w, const Consts &c, const float4 *planes_state, int nq, const lfd_query *q,
                          float *out, cudaStream_t st);
 }  // namespace lfd
