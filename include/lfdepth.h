@@ -12,6 +12,11 @@
  *    0..H-1), x right, y down, z forward.  K must be pinhole (last row 0 0 1).
  *  - Colours are RGB in [0,1]: RGBA8 texels are value/255; the alpha channel
  *    is ignored.
+ *  - A point projected into view i at (x, y) lies in that view iff it is in
+ *    front of both cameras and -1/2 <= x < W - 1/2, -1/2 <= y < H - 1/2 (the
+ *    image's texture area: its nearest pixel floor(x + 1/2), floor(y + 1/2)
+ *    is a pixel of view i).  Bilinear samples clamp the coordinates to the
+ *    outermost pixel centres (clamp to edge).
  *  - Superpixels: label maps are row-major int32 H x W per view with values in
  *    [0, grid_w * grid_h); label = gy * grid_w + gx places the superpixel on a
  *    regular grid whose 8-neighbourhood is the paper's neighbour system

@@ -20,10 +20,14 @@
  * Readings of points the paper leaves open (each one also a flag):
  *  - SSD of a pixel (Eq. 1): sum over R,G,B of squared differences, values in
  *    [0,1]; the superpixel is the patch.
- *  - sub-pixel sampling: TSSD uses bilinear interpolation, valid iff
- *    0 <= x <= W-1, 0 <= y <= H-1 (second tap index clamped) and the point is
- *    in front of both cameras; Eq. 9/10 use the nearest pixel floor(x+0.5)
- *    with the same window.
+ *  - sub-pixel sampling: a projection (x, y) lies in view i iff it is in
+ *    front of both cameras and on the image's texture area,
+ *    -1/2 <= x < W - 1/2 and -1/2 <= y < H - 1/2 (pixel centres at integers),
+ *    i.e. iff its nearest pixel floor(x + 1/2), floor(y + 1/2) is a pixel of
+ *    view i; TSSD samples bilinearly with the coordinates clamped to the
+ *    outermost pixel centres (clamp to edge), Eq. 9/10 take that nearest
+ *    pixel.  This is the domain of a texture sampled by GLSL, the paper's
+ *    implementation (Section III-E).
  *  - out-of-view pixels: sweep adds T; refinement leaves them out of view i's
  *    sums; V_i = O_i = 0 when no pixel projects validly; V_i = 0 when X is
  *    empty; the 1/N of Eq. 8 counts every neighbour view.
@@ -498,22 +502,25 @@ int32_t orc_project_pixel(void *h, int32_t v, int32_t k, double d, double nx, do
 
 static int in_window(const orc_view *wi, double x, double y)
 {
-    return x >= 0.0 && x <= (double)(wi->W - 1) && y >= 0.0 && y <= (double)(wi->H - 1);
+    return x >= -0.5 && x < (double)wi->W - 0.5 && y >= -0.5 && y < (double)wi->H - 0.5;
 }
 
 /* within `m` pixels of a window edge, so that FP32 could decide the other way */
 static int near_window_edge(const orc_view *wi, double x, double y, double m)
 {
-    double xm = (double)(wi->W - 1), ym = (double)(wi->H - 1);
-    int xin = x > -m && x < xm + m, yin = y > -m && y < ym + m;
-    int xe = fabs(x) < m || fabs(x - xm) < m;
-    int ye = fabs(y) < m || fabs(y - ym) < m;
+    double x0 = -0.5, y0 = -0.5, x1 = (double)wi->W - 0.5, y1 = (double)wi->H - 0.5;
+    int xin = x > x0 - m && x < x1 + m, yin = y > y0 - m && y < y1 + m;
+    int xe = fabs(x - x0) < m || fabs(x - x1) < m;
+    int ye = fabs(y - y0) < m || fabs(y - y1) < m;
     return (xe && yin) || (ye && xin);
 }
 
-/* bilinear interpolation of view colour at (x,y), 0<=x<=W-1, 0<=y<=H-1 */
+/* bilinear interpolation of view colour at (x,y), the coordinates clamped to
+ * [0, W-1] x [0, H-1] first (clamp to edge) */
 static void bilinear(const orc_view *wi, double x, double y, double *out)
 {
+    x = x < 0.0 ? 0.0 : (x > (double)(wi->W - 1) ? (double)(wi->W - 1) : x);
+    y = y < 0.0 ? 0.0 : (y > (double)(wi->H - 1) ? (double)(wi->H - 1) : y);
     int x0 = (int)floor(x), y0 = (int)floor(y);
     int x1 = x0 + 1 < wi->W ? x0 + 1 : wi->W - 1;
     int y1 = y0 + 1 < wi->H ? y0 + 1 : wi->H - 1;
@@ -537,8 +544,6 @@ void orc_bilinear_image(const double *rgb, int32_t W, int32_t H, double x, doubl
 /* ------------------------------------------------------------------------ */
 /* photo-consistency of the sweep: Eq. 1 and the inner sums of Eq. 2       */
 /* ------------------------------------------------------------------------ */
-
-static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
 /* truncated SSD between the reference pixel colour and view i sampled at (x,y) */
 static double tssd_at(const orc_ctx *c, const orc_view *wi, const double *ref, double x, double y)
@@ -569,7 +574,7 @@ static double tssd_cost(const orc_ctx *c, const orc_view *w, int s, const double
             double nominal = valid ? tssd_at(c, wi, ref, pr.x, pr.y) : T;
             cost += nominal;
             if (pr.front && near_window_edge(wi, pr.x, pr.y, m)) {
-                double alt = tssd_at(c, wi, ref, clampd(pr.x, 0, wi->W - 1), clampd(pr.y, 0, wi->H - 1));
+                double alt = tssd_at(c, wi, ref, pr.x, pr.y);      /* sampled as if inside */
                 clo += alt < T ? alt : T;
                 chi += T;
                 *flag = 1;

@@ -189,10 +189,11 @@ cudaError_t launch_rasterize(const Workspace &w, const Consts &c, float *const *
 
 struct alignas(16) SpView {
     float hw_a, qw, Ex, Dx;
-    float Ey, Dy, lo_x, hi_x;            // window of fx: [-xa, Wi-1-xa]
+    float Ey, Dy;
+    int xa_m, ya_m;                      // anchor pixel minus the bits of 1.5 * 2^23 (see energy_sample)
     float Pp00, Pp01, Pp10, Pp11;        // P00 - xa P20, P01 - xa P21, P10 - ya P20, P11 - ya P21
-    float P20, P21, lo_y, hi_y;
-    int xa, ya, Wi, pad;
+    float P20, P21;
+    int Wi, Hi;
     const float4 *map;
     long long pad2;
 };
@@ -253,9 +254,9 @@ struct Acc {
 };
 
 struct ViewK {
-    float hw, a20, a21, cx, b0, b1, cy, c0, c1, lo_x, hi_x, lo_y, hi_y;
+    float hw, a20, a21, cx, b0, b1, cy, c0, c1;
     float xy;
-    int xa, ya, Wi;
+    int xa_m, ya_m, Wi, Hi;
     const float4 *map;
 };
 
@@ -333,10 +334,15 @@ __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du
     const float ey = fmaf(K.c0, du, fmaf(K.c1, dv, K.cy));
     const float r = rcp_approx(Nw);
     const float fx = ex * r, fy = ey * r;                        // offsets from the integer anchor
-    const bool ok = act && (gp > 0.f) && (Nw > 0.f) && (fx >= K.lo_x) && (fx <= K.hi_x) && (fy >= K.lo_y) &&
-                    (fy <= K.hi_y);
-    const int ix = K.xa + __float2int_rd(fx + 0.5f);             // nearest pixel floor(x + 0.5)
-    const int iy = K.ya + __float2int_rd(fy + 0.5f);
+    // Nearest pixel: adding 1.5 * 2^23 rounds an offset |f| < 2^22 to an
+    // integer held in the low mantissa bits (ties to even: the oracle flags
+    // an exact .5 as a rounding boundary where either pixel is admissible).
+    // The point lies in view i iff that pixel does (-1/2 <= x < W - 1/2);
+    // out-of-range or non-finite offsets give out-of-range integers.
+    const int ix = __float_as_int(fx + 12582912.0f) + K.xa_m;
+    const int iy = __float_as_int(fy + 12582912.0f) + K.ya_m;
+    const bool ok = act && (gp > 0.f) && (Nw > 0.f) && ((unsigned)ix < (unsigned)K.Wi) &&
+                    ((unsigned)iy < (unsigned)K.Hi);
     const int idx = ok ? iy * K.Wi + ix : 0;                     // in-bounds address either way
     const float4 t = __ldg(K.map + idx);
     const float dr = t.x - cr, dg = t.y - cg, db = t.z - cb;
@@ -395,8 +401,7 @@ __device__ __noinline__ void view_terms(const Workspace &w, unsigned mask, float
             K.c1 = fmaf(sv.Dy, h.g1, sv.Pp11);
             K.a20 = fmaf(sv.qw, h.g0, sv.P20);
             K.a21 = fmaf(sv.qw, h.g1, sv.P21);
-            K.lo_x = sv.lo_x; K.hi_x = sv.hi_x; K.lo_y = sv.lo_y; K.hi_y = sv.hi_y;
-            K.xa = sv.xa; K.ya = sv.ya; K.Wi = sv.Wi;
+            K.xa_m = sv.xa_m; K.ya_m = sv.ya_m; K.Wi = sv.Wi; K.Hi = sv.Hi;
             K.map = sv.map;
             K.xy = DOMAIN == 0 ? sh.xy_lo : sh.xy_hi;
             Acc a = {0u, 0u, 0u, 0.f, 0.f};
@@ -567,15 +572,11 @@ __device__ bool setup_sp(const Workspace &w, const float4 *planes_in, int gs, in
         sv.Pp11 = (float)((pd.P[4] - ya * pd.P[7]) * rs);
         sv.P20 = (float)(pd.P[6] * rs);
         sv.P21 = (float)(pd.P[7] * rs);
-        sv.xa = (int)xa;
-        sv.ya = (int)ya;
+        sv.xa_m = (int)xa - 0x4B400000;      // |xa| <= 2^20: no overflow
+        sv.ya_m = (int)ya - 0x4B400000;
         sv.Wi = pd.Wi;
-        sv.lo_x = (float)(-xa);
-        sv.hi_x = (float)(pd.Wi - 1 - xa);
-        sv.lo_y = (float)(-ya);
-        sv.hi_y = (float)(pd.Hi - 1 - ya);
+        sv.Hi = pd.Hi;
         sv.map = pd.map_i;
-        sv.pad = 0;
         sv.pad2 = 0;
         sh.view[lane] = sv;
     }

@@ -105,15 +105,19 @@ __device__ __forceinline__ float3 texel_colour(const void *tex, long long idx, l
 
 // Truncated SSD of Eq. 1 between the reference colour `ref` and view i sampled
 // bilinearly at the homogeneous point (X, Y, Wz); T when the point is behind
-// camera i (Wz <= 0) or outside 0 <= x <= Wi-1, 0 <= y <= Hi-1.
+// camera i (Wz <= 0) or off the image's texture area -1/2 <= x < Wi - 1/2,
+// -1/2 <= y < Hi - 1/2 (its nearest pixel is not a pixel of view i).  Inside,
+// the coordinates are clamped to the outermost pixel centres (clamp to edge).
 template <int FMT>
 __device__ __forceinline__ float tssd_sample(const void *tex, int Wi, int Hi, float X, float Y, float Wz, float3 ref,
                                              float T)
 {
     const float rw = rcp_approx(Wz);
-    const float x = X * rw, y = Y * rw;
-    const bool ok = (Wz > 0.f) && (x >= 0.f) && (x <= (float)(Wi - 1)) && (y >= 0.f) && (y <= (float)(Hi - 1));
+    const float xr = X * rw, yr = Y * rw;
+    const bool ok = (Wz > 0.f) && (xr >= -0.5f) && (xr < (float)Wi - 0.5f) && (yr >= -0.5f) &&
+                    (yr < (float)Hi - 0.5f);
     if (!ok) return T;
+    const float x = fminf(fmaxf(xr, 0.f), (float)(Wi - 1)), y = fminf(fmaxf(yr, 0.f), (float)(Hi - 1));
     const float xf = floorf(x), yf = floorf(y);
     const float fx = x - xf, fy = y - yf;
     const long long idx = (long long)(int)yf * Wi + (int)xf;

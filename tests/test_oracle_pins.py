@@ -171,6 +171,8 @@ def test_bilinear_is_scipy_order1_interpolation():
     rng = np.random.default_rng(2)
     img = rng.uniform(size=(13, 17, 3))
     pts = list(zip(rng.uniform(0, 16, 50), rng.uniform(0, 12, 50))) + [(16.0, 12.0), (16.0, 3.3), (0.0, 0.0), (7.25, 12.0)]
+    # the half-pixel margin of the texture area: clamp to edge (scipy's mode "nearest")
+    pts += [(-0.5, 4.2), (-0.25, -0.5), (16.49, 12.3), (3.7, 12.499), (16.2, -0.3)]
     for x, y in pts:
         got = orc.bilinear_image(img, x, y)
         ref = [ndimage.map_coordinates(img[..., ch], [[y], [x]], order=1, mode="nearest")[0] for ch in range(3)]
@@ -405,11 +407,9 @@ def test_identity_view_gives_unit_consistency_and_zero_cost():
             st[o.sp_base[v] + s] = [rho / (n @ ray), *n]
     for s in (0, 8, 23):
         r = o.score(st, [(0, s, *st[s])])[0]
-        # border pixels map onto the window edge itself: a flagged decision whose
-        # in-window outcome costs 0; interior superpixels are exactly 0
-        assert r["tssd_lo"] < 1e-20
-        if s == 8:
-            assert r["tssd"] < 1e-20 and r["flag_tssd"] == 0
+        # border pixels map onto the outermost pixel centres, half a pixel inside
+        # the texture area: nothing is flagged and the cost is exactly 0
+        assert r["tssd"] < 1e-20 and r["flag_tssd"] == 0 and r["tssd_hi"] < 1e-20
         assert abs(r["S"][0] - 1) < 1e-12 and abs(r["Vt"][0] - 1) < 1e-12 and r["O"][0] == 0
         assert abs(r["E"] - 1) < 1e-12
 
