@@ -27,7 +27,25 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define SLIC_MARGIN 1e-4   /* relative gap between the two smallest D^2 below which a pixel is flagged */
+/* Flag margin of an assignment, derived from the FP32 arithmetic an
+ * implementation may use.  Its CIELAB conversion of a pixel (sRGB power,
+ * matrix, cube root: a few ulp on f in [0, 1], times 116, 500 and 200 in
+ * L, a, b) leaves each Lab vector within SLIC_LAB_EPS of this FP64 value
+ * (about 3e-5 in L, 2.1e-4 in a, 8e-5 in b for 4-ulp power and 1-ulp cube
+ * root; rounded up).  A distance D^2 = |Lab - Lab_c|^2 + w |xy - xy_c|^2
+ * then moves by at most 2 |Lab - Lab_c| eps + eps^2 <= 2 sqrt(D^2) eps + eps^2,
+ * and the FP32 rounding of the sum adds at most 8 u D^2 (u = 2^-24).  Two
+ * candidates can swap only when their gap is below the sum of both bounds;
+ * such pixels are flagged. */
+#define SLIC_LAB_EPS 4e-4
+#define SLIC_U 5.9604644775390625e-08
+
+static int slic_near_tie(double best, double second)
+{
+    if (!isfinite(second)) return 0;
+    const double e = SLIC_LAB_EPS;
+    return (second - best) <= 2.0 * e * (sqrt(best) + sqrt(second)) + 2.0 * e * e + 8.0 * SLIC_U * (best + second);
+}
 
 static double srgb_to_linear(double c)
 {
@@ -82,7 +100,7 @@ void orc_slic_seeds(int32_t W, int32_t H, const double *rgb, int32_t GW, int32_t
 }
 
 /* one assignment step from `centres`; flags (nullable): 1 where the two
- * smallest distances are within SLIC_MARGIN (relative) */
+ * smallest distances are a near tie (slic_near_tie) */
 void orc_slic_assign(int32_t W, int32_t H, const double *rgb, int32_t GW, int32_t GH, const double *centres,
                      double m, int32_t *labels, uint8_t *flags)
 {
@@ -117,7 +135,7 @@ void orc_slic_assign(int32_t W, int32_t H, const double *rgb, int32_t GW, int32_
                     }
                 }
             labels[(size_t)y * W + x] = arg;
-            if (flags) flags[(size_t)y * W + x] = (second - best) <= SLIC_MARGIN * (best + 1.0);
+            if (flags) flags[(size_t)y * W + x] = (uint8_t)slic_near_tie(best, second);
         }
     }
     free(bx);
