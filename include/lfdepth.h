@@ -466,8 +466,14 @@ lfd_status lfd_get_superpixels(lfd_ctx *ctx, int32_t view, int32_t *offsets, int
  * b, minw, count, 0} for every label s < grid_w*grid_h (device float array of
  * grid_w*grid_h*8, caller-owned).  labels: device int32 width x height,
  * row-major; image: device texels of `fmt` with pitch_bytes per row (0 = tight);
- * alpha: the colour width of Eq. 7 used for minw.  Labels outside the grid are
- * ignored.  Asynchronous on `stream`; allocates nothing.
+ * alpha: colour width used for minw (the same value as lfd_params.alpha).
+ * Labels outside [0, grid_w*grid_h) are ignored (the regular path rejects
+ * them).  An empty label reports what lfd_get_superpixels reports for it:
+ * centroid and colour 0, count 0, and as minw the smallest similarity of
+ * colour 0 to its non-empty neighbours (1 if none).  Asynchronous on
+ * `stream`; allocates nothing.  LFD_ERR_CUDA only when one of this call's
+ * launches fails; an error pending on the calling thread from earlier work
+ * is left as it is.
  *
  * Its scratch (per-label counts and bounding boxes) is a fixed device array of
  * LFD_NOALLOC_MAX_LABELS entries (1.25 MiB) that every GPU which loads the

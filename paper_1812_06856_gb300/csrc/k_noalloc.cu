@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(256) k_na_stats(const NoallocScratch *sc, cons
     __shared__ double shd[256];
     __shared__ long long shl[256];
     float *out = stats + 8 * (long long)s;
-    if (n == 0) {
-        if (threadIdx.x < 8) out[threadIdx.x] = 0.f;
+    if (n == 0) {   // as the regular path: centroid and colour 0, minw filled in by k_na_minw
+        if (threadIdx.x < 8) out[threadIdx.x] = threadIdx.x == 5 ? 1.f : 0.f;
         return;
     }
     const int4 bb = sc->bbox[s];
@@ -146,13 +146,14 @@ __global__ void __launch_bounds__(256) k_na_stats(const NoallocScratch *sc, cons
     }
 }
 
-// minimum colour similarity to the present 8-neighbours (Eq. 11), from the colours just written
+// minimum colour similarity to the present (non-empty) 8-neighbours, from the
+// colours just written; an empty label gets the value the regular path gives
+// it (its colour is 0), so both report the same slot 5 for every label
 __global__ void k_na_minw(float *stats, int GW, int GH, double k_col)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= GW * GH) return;
     const float *me = stats + 8 * (long long)s;
-    if (me[6] == 0.f) return;
     const int gx = s % GW, gy = s / GW;
     const int dxs[8] = {1, 1, 0, -1, -1, -1, 0, 1}, dys[8] = {0, -1, -1, -1, 0, 1, 1, 1};
     double best = 1.0;
@@ -206,10 +207,24 @@ extern "C" lfd_status lfd_superpixel_stats_noalloc(const int32_t *labels, const 
     cudaStream_t st = (cudaStream_t)stream;
     const int S = grid_w * grid_h;
     const int npx = width * height;
-    k_na_clear<<<(S + 255) / 256, 256, 0, st>>>(sc, S);
-    k_na_count<<<(npx + 255) / 256, 256, 0, st>>>(sc, labels, width, height, S);
-    k_na_stats<<<S, 256, 0, st>>>(sc, labels, image, pitch, fmt, width, stats_out);
+    // An error left pending on this thread by earlier, unrelated work is not
+    // this call's: a launch of this call has failed only when the pending
+    // error changes from what it was on entry.  (The earlier error stays
+    // pending for its owner.)
+    const cudaError_t before = cudaPeekAtLastError();
+    auto launch_failed = [before]() {
+        const cudaError_t e = cudaPeekAtLastError();
+        return e != cudaSuccess && e != before;
+    };
     const double log2e = 1.4426950408889634;
-    k_na_minw<<<(S + 127) / 128, 128, 0, st>>>(stats_out, grid_w, grid_h, log2e / (2.0 * alpha * alpha));
-    return cudaGetLastError() == cudaSuccess ? LFD_OK : LFD_ERR_CUDA;
+    k_na_clear<<<(S + 255) / 256, 256, 0, st>>>(sc, S);
+    if (!launch_failed()) k_na_count<<<(npx + 255) / 256, 256, 0, st>>>(sc, labels, width, height, S);
+    if (!launch_failed()) k_na_stats<<<S, 256, 0, st>>>(sc, labels, image, pitch, fmt, width, stats_out);
+    if (!launch_failed())
+        k_na_minw<<<(S + 127) / 128, 128, 0, st>>>(stats_out, grid_w, grid_h, log2e / (2.0 * alpha * alpha));
+    if (launch_failed()) {
+        if (before == cudaSuccess) cudaGetLastError();   // clear only what this call raised
+        return LFD_ERR_CUDA;
+    }
+    return LFD_OK;
 }

@@ -192,11 +192,30 @@ def kernel_offsets(size_init: int, steps_init: int, it: int) -> np.ndarray:
 def superpixel_stats_noalloc(labels: torch.Tensor, image: torch.Tensor, grid_w: int, grid_h: int, alpha: float,
                              stats_out: torch.Tensor, stream=None) -> None:
     """lfd_superpixel_stats_noalloc on one view: labels (H,W) int32 and image
-    (H,W,4) on the device, stats_out (grid_w*grid_h, 8) float32 on the device."""
+    (H,W,4) texels on the device, stats_out (grid_w*grid_h, 8) float32 on the
+    device.  The image may have padded rows (row stride >= W texels); its
+    texels must be packed within a row.  Raises ValueError for arguments the
+    call cannot take safely, LfdError for a status other than LFD_OK."""
     lib = load()
+    if not (isinstance(labels, torch.Tensor) and isinstance(image, torch.Tensor) and isinstance(stats_out, torch.Tensor)):
+        raise ValueError("labels, image and stats_out must be torch tensors")
+    if not (labels.is_cuda and image.is_cuda and stats_out.is_cuda):
+        raise ValueError("labels, image and stats_out must be CUDA tensors")
+    if not (labels.device == image.device == stats_out.device):
+        raise ValueError("labels, image and stats_out must be on one device")
+    if labels.dtype != torch.int32 or labels.dim() != 2 or not labels.is_contiguous():
+        raise ValueError("labels must be a contiguous (H, W) int32 tensor")
     H, W = int(labels.shape[0]), int(labels.shape[1])
+    if image.dtype not in _DTYPE_FMT or image.dim() != 3 or tuple(image.shape) != (H, W, 4):
+        raise ValueError(f"image must be (H, W, 4) = ({H}, {W}, 4) of uint8/float16/bfloat16/float32")
+    if image.stride(2) != 1 or image.stride(1) != 4 or image.stride(0) < 4 * W:
+        raise ValueError("image texels must be packed within each row (strides (>= 4W, 4, 1))")
+    if stats_out.dtype != torch.float32 or not stats_out.is_contiguous() or \
+            stats_out.numel() < int(grid_w) * int(grid_h) * 8:
+        raise ValueError("stats_out must be a contiguous float32 tensor of at least grid_w * grid_h * 8 elements")
     fmt = _DTYPE_FMT[image.dtype]
-    st = lib.lfd_superpixel_stats_noalloc(labels.data_ptr(), image.data_ptr(), W, H, W * _TEXEL[fmt], fmt,
+    pitch = image.stride(0) * image.element_size()
+    st = lib.lfd_superpixel_stats_noalloc(labels.data_ptr(), image.data_ptr(), W, H, pitch, fmt,
                                           int(grid_w), int(grid_h), float(alpha), stats_out.data_ptr(),
                                           _stream(stream))
     if st != 0:
