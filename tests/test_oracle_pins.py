@@ -614,3 +614,38 @@ def test_perturbation_only_adds_candidates_and_its_winners_are_samples():
     keep = won & np.isfinite(prop_d)
     rel = np.abs(rk["planes"][keep, 0] / prop_d[keep] - 1.0)
     assert np.all(rel <= rad * (1 + 1e-12))
+
+
+def test_recovery_is_exact_for_fronto_planes_at_bin_centres():
+    """The recovery floor is the sampling, not the method: with the jitter off
+    and config 1's fronto-parallel planes moved to inverse-depth bin centres,
+    the sweep lands on their exact depth and the iterations keep it, so the
+    median relative inverse-depth error on their superpixels is 0 (the benchmark spec
+    target 1e-3); the slanted planes, whose normals come only from the
+    triangles of neighbouring centroids (Fig. 3b), stay near 1 %."""
+    import dataclasses
+    lf = synth.make_config(1)
+    p = synth.method_params(lf, jitter=0)
+    d_min, d_max, L = p["d_min"], p["d_max"], p["num_labels"]
+    delta = (1 / d_min - 1 / d_max) / L
+    planes = []
+    for q in lf.scene.planes:
+        q2 = synth.PlaneObj(**{**q.__dict__})
+        if np.allclose(np.abs(q.normal), [0, 0, 1]):
+            k = int(np.floor((1 / q.centre[2] - 1 / d_max) / delta))
+            q2.centre = np.array([q.centre[0], q.centre[1], 1 / (1 / d_max + (k + 0.5) * delta)])
+        planes.append(q2)
+    scene = synth.Scene(planes, list(lf.scene.spheres))
+    rgb, depth, obj = synth.render(lf.rig, scene)
+    lf2 = dataclasses.replace(lf, scene=scene, rgb=rgb, depth=depth, obj=obj)
+    o = orc.Oracle(*synth.oracle_inputs(lf2, synth.rgba8_as_float(synth.quantize_rgba8(rgb))), p)
+    gt = synth.gt_planes(lf2).reshape(-1, 4)
+    fronto = (gt[:, 0] > 0) & np.isclose(np.abs(gt[:, 3]), 1.0)
+    slanted = (gt[:, 0] > 0) & ~fronto
+    assert fronto.sum() > 500 and slanted.sum() > 50
+    planes_out, hist = o.run()
+    for pl in hist:
+        err = np.abs(1 / pl[fronto, 0] - 1 / gt[fronto, 0]) * gt[fronto, 0]
+        assert np.median(err) < 1e-12
+    err_s = np.abs(1 / planes_out[slanted, 0] - 1 / gt[slanted, 0]) * gt[slanted, 0]
+    assert 1e-3 < np.median(err_s) < 0.05
