@@ -150,7 +150,8 @@ typedef struct lfd_ctx lfd_ctx;
 
 int32_t lfd_version(void);
 /* ABI check for bindings: writes sizeof(lfd_camera), sizeof(lfd_lightfield),
- * sizeof(lfd_params), sizeof(lfd_query), sizeof(lfd_batch_options) into out[0..4]. */
+ * sizeof(lfd_params), sizeof(lfd_query), sizeof(lfd_batch_options),
+ * sizeof(lfd_result) into out[0..5]. */
 void lfd_struct_sizes(int32_t *out);
 const char *lfd_status_string(lfd_status s);
 void lfd_params_default(lfd_params *p);
@@ -331,6 +332,21 @@ lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs
                               float *const *const *planes_out, float *const *const *depth_out,
                               const lfd_batch_options *options, void *stream);
 
+/* lfd_estimate_batch with warm starts (the frames of rigs whose previous
+ * planes are kept, as a frame server does; the paper processes every light
+ * field from scratch).  warm_planes: host array [n]; entry l is NULL (light
+ * field l starts cold from the plane sweep) or a host array [V_l] of device
+ * float4[S_v] planes it starts from instead: it takes no part in the sweep
+ * and runs params[l].iterations iterations with params[l].warm_iter_offset
+ * added to I (Eq. 4).  warm_planes itself may be NULL (all cold; the same
+ * as lfd_estimate_batch).  Warm planes are read before planes_out is
+ * written, so warm_planes[l][v] may equal planes_out[l][v].  Results equal n
+ * separate lfd_estimate calls with the same warm planes.  options->graph
+ * must be 0 when any light field is warm.  Asynchronous. */
+lfd_status lfd_estimate_batch_warm(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs, const lfd_params *params,
+                                   const float *const *const *warm_planes, float *const *const *planes_out,
+                                   float *const *const *depth_out, const lfd_batch_options *options, void *stream);
+
 /* Device workspace (bytes) that binding these n light fields allocates: the
  * figure lfd_create's hbm_budget_bytes is checked against.  Reads only the
  * cameras, grid sizes and pixel format. */
@@ -343,9 +359,15 @@ lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out);
 /* ---- serving ---------------------------------------------------------- */
 
 /* A frame server: several rigs (camera arrays, each a stream of light-field
- * frames) share one GPU.  A server owns `max_slots` slots, each a context with
- * its own CUDA stream; frames of different rigs run concurrently on different
- * slots, frames of one rig run in submission order on the rig's slot.
+ * frames) share one GPU by continuous batching.  Submitted frames wait in one
+ * queue in arrival order.  A dispatcher thread owned by the server watches
+ * `max_slots` slots (a context and a CUDA stream each); whenever a slot is
+ * free it takes every queued frame that can run now -- at most one frame per
+ * rig, from rigs with no frame on the device, all warm or all cold, as many
+ * as the HBM budget allows -- and runs them as one lfd_estimate_batch_warm
+ * call on that slot's stream.  Frames that arrive while batches run join the
+ * next batch a freed slot forms; frames of one rig run in submission order.
+ * Each frame's result is the same whether it ran alone or in a batch.
  *
  * Warm start (not in the paper, where every frame is independent): the first
  * frame of a rig (or the first after its layout changes) runs the plane sweep
@@ -354,13 +376,17 @@ lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out);
  * warm_iter_offset added to the iteration index of Eq. 4 (defaults 3 and 3:
  * the small kernels of I = 4..6).  warm_iterations = 0 makes every frame cold.
  *
- * Admission: a rig is bound to the slot with the fewest rigs when first seen;
- * a slot's workspace is the largest lfd_workspace_required() of its rigs; the
- * sum over slots plus the rigs' plane states must stay within
+ * Admission: a frame is accepted when its own workspace
+ * (lfd_workspace_required) plus every rig's plane state fits
  * hbm_budget_bytes (0 = no bound), else the submit fails with LFD_ERR_BUDGET.
- * At most max_pending_per_rig frames of a rig may be in flight; a submit
- * beyond that returns LFD_ERR_BUSY (the caller drops or retries the frame).
- * The server is not thread safe. */
+ * A batch is formed only while the workspace it needs, the workspaces the
+ * other slots hold (each keeps the largest it has used) and the plane states
+ * fit the budget; frames that do not fit wait for a later batch (a frame that
+ * fits no slot while every slot is idle completes with LFD_ERR_BUDGET).  At
+ * most max_pending_per_rig frames of a rig may be submitted and not yet
+ * polled; a submit beyond that returns LFD_ERR_BUSY (the caller drops or
+ * retries the frame).  Server calls may come from one caller thread at a
+ * time. */
 typedef struct lfd_server lfd_server;
 
 typedef struct {
@@ -369,9 +395,12 @@ typedef struct {
     int32_t warm;              /* 1: started from the rig's previous planes */
     int64_t frame;             /* 0-based frame count of the rig */
     int64_t submit_ns;         /* lfd_server_now_ns() at submission */
-    int64_t done_ns;           /* lfd_server_now_ns() when the stream reached the end of the frame */
+    int64_t done_ns;           /* lfd_server_now_ns() when the stream reached the end of its batch */
     lfd_status status;
-    int32_t slot;
+    int32_t slot;              /* slot whose stream ran the frame */
+    int64_t start_ns;          /* lfd_server_now_ns() when its batch was launched */
+    int32_t batch;             /* frames in that batch */
+    int32_t reserved;
 } lfd_result;
 
 lfd_status lfd_server_create(lfd_server **out, int32_t device, uint64_t hbm_budget_bytes, int32_t max_slots);
@@ -380,6 +409,11 @@ const char *lfd_server_last_error(const lfd_server *srv);
 /* Warm-start schedule and queue bound (defaults 3, 3, 2). */
 lfd_status lfd_server_configure(lfd_server *srv, int32_t warm_iterations, int32_t warm_iter_offset,
                                 int32_t max_pending_per_rig);
+/* Largest number of frames in one batch (0 = no limit, the default; 1 runs
+ * every frame on its own). */
+lfd_status lfd_server_set_max_batch(lfd_server *srv, int32_t max_frames);
+/* Batches launched and frames they held since the server was created. */
+lfd_status lfd_server_stats(lfd_server *srv, int64_t *batches, int64_t *frames);
 /* Monotonic clock of the result timestamps, in ns. */
 int64_t lfd_server_now_ns(void);
 
@@ -395,8 +429,9 @@ lfd_status lfd_server_submit(lfd_server *srv, int32_t rig_id, const lfd_lightfie
  * running; LFD_ERR_INVALID_ARG for an unknown id. */
 lfd_status lfd_server_poll(lfd_server *srv, uint64_t req_id, int32_t timeout_us, lfd_result *out);
 /* The plane state of rig `rig_id` (all views' superpixels in order, float4
- * each) to host memory after its queued frames (synchronous); *n_sp gets
- * the superpixel count; planes_host may be NULL to query it. */
+ * each) to host memory once its queued frames have run (synchronous; waits
+ * up to a minute, then LFD_ERR_TIMEOUT); *n_sp gets the superpixel count;
+ * planes_host may be NULL to query it. */
 lfd_status lfd_server_export_state(lfd_server *srv, int32_t rig_id, float *planes_host, int64_t cap_sp,
                                    int64_t *n_sp);
 /* Replace rig `rig_id`'s plane state (e.g. exported from another server);

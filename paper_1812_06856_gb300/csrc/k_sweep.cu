@@ -58,6 +58,7 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
 {
     const int v = __ldg(w.sp_view + gs);
     const ViewDev &vd = w.views[v];
+    if (vd.sweep_skip) return;               // warm-started view: its planes are given
     const int s = gs - vd.sp_base;
     const int n = __ldg(w.sp_cnt + gs);
     if (n == 0) {

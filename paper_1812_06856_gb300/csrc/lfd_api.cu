@@ -749,11 +749,14 @@ lfd_status need_bound(lfd_ctx *ctx)
     return LFD_OK;
 }
 
-lfd_status gather_planes(lfd_ctx *ctx, const float *const *src, float4 *dst, cudaStream_t st)
+lfd_status gather_planes(lfd_ctx *ctx, const float *const *src, float4 *dst, cudaStream_t st, bool allow_null = false)
 {
     if (!src) return fail(ctx, LFD_ERR_INVALID_ARG, "planes array is NULL");
     for (int v = 0; v < ctx->L.V; v++) {
-        if (!src[v]) return fail(ctx, LFD_ERR_INVALID_ARG, "planes of view %d is NULL", v);
+        if (!src[v]) {
+            if (allow_null) continue;
+            return fail(ctx, LFD_ERR_INVALID_ARG, "planes of view %d is NULL", v);
+        }
         LFD_CUDA(cudaMemcpyAsync(dst + ctx->L.sp_base[v], src[v], 16 * (size_t)ctx->L.S[v], cudaMemcpyDeviceToDevice, st));
     }
     return LFD_OK;
@@ -830,16 +833,21 @@ int max_iterations(const lfd_ctx *ctx)
 }
 
 // The device work of one frame after the inputs are bound: sweep (or warm
-// planes), all iterations, final rasterisation, planes out.  Capturable.
+// planes), all iterations, final rasterisation, planes out.  warm: NULL (every
+// view cold) or one planes pointer per bound view, NULL for a cold view (the
+// sweep leaves out the views marked sweep_skip, whose planes are gathered
+// after it).  Capturable.
 lfd_status enqueue_frame(lfd_ctx *ctx, const float *const *warm, float *const *const *planes_out,
                          float *const *depth_dev, cudaStream_t st, cudaMemcpyKind out_kind)
 {
     lfd_status s;
-    if (warm) {
-        if ((s = gather_planes(ctx, warm, ctx->d_planesA, st)) != LFD_OK) return s;
-    } else {
+    bool all_warm = warm != nullptr;
+    if (warm)
+        for (int v = 0; v < ctx->L.V; v++) all_warm = all_warm && warm[v] != nullptr;
+    if (!all_warm)
         if ((s = run_sweep(ctx, nullptr, st)) != LFD_OK) return s;
-    }
+    if (warm)
+        if ((s = gather_planes(ctx, warm, ctx->d_planesA, st, true)) != LFD_OK) return s;
     float4 *a = ctx->d_planesA, *b = ctx->d_planesB;
     const int iters = max_iterations(ctx);
     for (int it = 1; it <= iters; it++) {
@@ -1008,6 +1016,7 @@ void lfd_struct_sizes(int32_t *out)
     out[2] = (int32_t)sizeof(lfd_params);
     out[3] = (int32_t)sizeof(lfd_query);
     out[4] = (int32_t)sizeof(lfd_batch_options);
+    out[5] = (int32_t)sizeof(lfd_result);
 }
 
 const char *lfd_status_string(lfd_status s)
@@ -1283,9 +1292,15 @@ lfd_status lfd_estimate_host(lfd_ctx *ctx, const lfd_lightfield *lf_host, const 
     return LFD_OK;
 }
 
-lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs, const lfd_params *params,
-                              float *const *const *planes_out, float *const *const *depth_out,
-                              const lfd_batch_options *options, void *stream)
+}  // extern "C"
+
+namespace {
+
+// lfd_estimate_batch and lfd_estimate_batch_warm: warm = NULL (every light
+// field cold) or per light field NULL / its views' warm planes
+lfd_status estimate_batch_impl(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs, const lfd_params *params,
+                               const float *const *const *warm, float *const *const *planes_out,
+                               float *const *const *depth_out, const lfd_batch_options *options, void *stream)
 {
     if (!ctx) return LFD_ERR_INVALID_ARG;
     ctx->err.clear();
@@ -1305,6 +1320,16 @@ lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs
         if (!lfs[l].num_views || lfs[l].num_views > LFD_MAX_VIEWS || !lfs[l].cams || !lfs[l].views || !lfs[l].labels ||
             !lfs[l].grid_w || !lfs[l].grid_h)
             return fail(ctx, LFD_ERR_INVALID_ARG, "light field %d is incomplete", l);
+    bool any_warm = false;
+    if (warm)
+        for (int l = 0; l < n; l++)
+            if (warm[l]) {
+                any_warm = true;
+                for (int v = 0; v < lfs[l].num_views; v++)
+                    if (!warm[l][v]) return fail(ctx, LFD_ERR_INVALID_ARG, "warm planes of light field %d view %d "
+                                                 "are NULL", l, v);
+            }
+    if (any_warm && o.graph) return fail(ctx, LFD_ERR_INVALID_ARG, "warm-started batches are not graph-captured");
     const uint64_t sig = batch_signature(n, lfs, params, planes_out, depth_out, &o);
 
     if (o.graph && ctx->gexec && ctx->gsig == sig && ctx->bound) {     // replay
@@ -1335,10 +1360,25 @@ lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs
     }
 
     if (!o.graph) {
+        std::vector<const float *> warm_flat;
+        if (any_warm) {
+            // views of warm light fields leave the sweep out (their records are
+            // still in the pinned staging buffer, uploaded by enqueue_input)
+            warm_flat.assign(total_views, nullptr);
+            ViewDev *hv = (ViewDev *)ctx->stage.buf();
+            for (int l = 0, g = 0; l < n; l++)
+                for (int v = 0; v < lfs[l].num_views; v++, g++)
+                    if (warm[l]) {
+                        warm_flat[g] = warm[l][v];
+                        hv[g].sweep_skip = 1;
+                    }
+        }
         if ((s = enqueue_input(ctx, st, true)) != LFD_OK) return s;
         float **dp = nullptr;
         if ((s = upload_depth_ptrs(ctx, depth_out ? depth_flat.data() : nullptr, st, &dp)) != LFD_OK) return s;
-        if ((s = enqueue_frame(ctx, nullptr, planes_out, dp, st, cudaMemcpyDeviceToDevice)) != LFD_OK) return s;
+        if ((s = enqueue_frame(ctx, any_warm ? warm_flat.data() : nullptr, planes_out, dp, st,
+                               cudaMemcpyDeviceToDevice)) != LFD_OK)
+            return s;
         ctx->bound = true;
         return LFD_OK;
     }
@@ -1397,6 +1437,24 @@ lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs
     LFD_CUDA(cudaEventRecord(ctx->ev_bdepth, st));
     ctx->bound = true;
     return LFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lfd_status lfd_estimate_batch(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs, const lfd_params *params,
+                              float *const *const *planes_out, float *const *const *depth_out,
+                              const lfd_batch_options *options, void *stream)
+{
+    return estimate_batch_impl(ctx, n, lfs, params, nullptr, planes_out, depth_out, options, stream);
+}
+
+lfd_status lfd_estimate_batch_warm(lfd_ctx *ctx, int32_t n, const lfd_lightfield *lfs, const lfd_params *params,
+                                   const float *const *const *warm_planes, float *const *const *planes_out,
+                                   float *const *const *depth_out, const lfd_batch_options *options, void *stream)
+{
+    return estimate_batch_impl(ctx, n, lfs, params, warm_planes, planes_out, depth_out, options, stream);
 }
 
 lfd_status lfd_workspace_required(int32_t n, const lfd_lightfield *lfs, uint64_t *bytes)

@@ -47,7 +47,7 @@ struct ViewDev {
     int L, jitter, lf_index, term_mask;
     int iters, warm_off;
     int lv;                  // index of the view within its light field (jitter key)
-    int pad2;
+    int sweep_skip;          // 1: the view starts from given (warm) planes; the sweep leaves it out
     unsigned long long seed;
     double inv_dmin, inv_dmax, delta;   // delta: inverse-depth bin width
     float T;                 // Eq. 1 truncation in the sampler's colour units squared

@@ -66,7 +66,8 @@ class BatchOptions(C.Structure):
 
 class Result(C.Structure):
     _fields_ = [("req_id", C.c_uint64), ("rig_id", C.c_int32), ("warm", C.c_int32), ("frame", C.c_int64),
-                ("submit_ns", C.c_int64), ("done_ns", C.c_int64), ("status", C.c_int32), ("slot", C.c_int32)]
+                ("submit_ns", C.c_int64), ("done_ns", C.c_int64), ("status", C.c_int32), ("slot", C.c_int32),
+                ("start_ns", C.c_int64), ("batch", C.c_int32), ("reserved", C.c_int32)]
 
 
 class LfdError(RuntimeError):
@@ -122,6 +123,8 @@ def load(build_if_missing: bool = True):
     lib.lfd_batch_options_default.argtypes = [P(BatchOptions)]
     lib.lfd_batch_options_default.restype = None
     lib.lfd_estimate_batch.argtypes = [vp, i32, P(LightFieldC), P(Params), P(vp), P(vp), P(BatchOptions), vp]
+    lib.lfd_estimate_batch_warm.argtypes = [vp, i32, P(LightFieldC), P(Params), P(vp), P(vp), P(vp),
+                                            P(BatchOptions), vp]
     lib.lfd_launch_config.argtypes = [vp, P(i32)]
     lib.lfd_workspace_required.argtypes = [i32, P(LightFieldC), P(C.c_uint64)]
     lib.lfd_fuse.argtypes = [vp, P(vp), P(vp), C.c_double, vp]
@@ -135,19 +138,23 @@ def load(build_if_missing: bool = True):
     lib.lfd_server_now_ns.restype = C.c_int64
     lib.lfd_server_submit.argtypes = [vp, i32, P(LightFieldC), P(Params), P(vp), P(vp), P(C.c_uint64)]
     lib.lfd_server_poll.argtypes = [vp, C.c_uint64, i32, P(Result)]
+    lib.lfd_server_set_max_batch.argtypes = [vp, i32]
+    lib.lfd_server_stats.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
     lib.lfd_server_export_state.argtypes = [vp, i32, vp, C.c_int64, P(C.c_int64)]
     lib.lfd_server_import_state.argtypes = [vp, i32, vp, C.c_int64]
     for name in ("lfd_create", "lfd_destroy", "lfd_set_input", "lfd_num_superpixels", "lfd_plane_sweep",
                  "lfd_rasterize", "lfd_iterate", "lfd_estimate", "lfd_estimate_host", "lfd_synchronize",
                  "lfd_counters", "lfd_score", "lfd_get_superpixels", "lfd_neighbor_views", "lfd_profile_enable",
-                 "lfd_profile_read", "lfd_estimate_batch", "lfd_launch_config", "lfd_workspace_required", "lfd_fuse", "lfd_slic",
+                 "lfd_profile_read", "lfd_estimate_batch", "lfd_estimate_batch_warm", "lfd_launch_config", "lfd_workspace_required", "lfd_fuse", "lfd_slic",
                  "lfd_server_create", "lfd_server_destroy", "lfd_server_configure", "lfd_server_submit",
-                 "lfd_server_poll", "lfd_server_export_state", "lfd_server_import_state"):
+                 "lfd_server_poll", "lfd_server_export_state", "lfd_server_import_state", "lfd_server_set_max_batch",
+                 "lfd_server_stats"):
         getattr(lib, name).restype = i32
     sizes = (i32 * 8)()
     lib.lfd_struct_sizes(sizes)
-    want = [C.sizeof(Camera), C.sizeof(LightFieldC), C.sizeof(Params), C.sizeof(Query), C.sizeof(BatchOptions)]
-    if list(sizes)[:5] != want:
+    want = [C.sizeof(Camera), C.sizeof(LightFieldC), C.sizeof(Params), C.sizeof(Query), C.sizeof(BatchOptions),
+            C.sizeof(Result)]
+    if list(sizes)[:6] != want:
         raise RuntimeError(f"lfdepth ABI mismatch: library struct sizes {list(sizes)} != binding {want}")
     _lib = lib
     return lib
@@ -401,13 +408,16 @@ class Context:
                     "lfd_estimate_host")
 
     def estimate_batch(self, items, options: dict | None = None, want_depth: bool = True, out=None,
-                       stream=None):
-        """Several light fields in one pass (lfd_estimate_batch).
+                       stream=None, warm=None):
+        """Several light fields in one pass (lfd_estimate_batch, or
+        lfd_estimate_batch_warm when `warm` is given).
 
         items: list of dicts with keys views, labels, K, R, t, GW, GH, params
         (as for `estimate`).  options: lfd_batch_options fields.  out: the
         (planes, depths) returned by an earlier call with the same items, to
         write into the same buffers (a graph replay needs identical pointers).
+        warm: None, or a list with one entry per item: None (cold) or a
+        (S_l, 4) float32 cuda tensor of that light field's warm planes.
         Returns (planes, depths): planes (S_total, 4) over all light fields'
         superpixels in order; depths a list of (V_l, H_l, W_l) tensors or None."""
         n = len(items)
@@ -459,8 +469,27 @@ class Context:
         for key, val in (options or {}).items():
             setattr(o, key, int(val))
         self._keep = [keep, lfs, ps, pp_all, pp, dd, o, planes, depths]
-        self._check(self.lib.lfd_estimate_batch(self.h, n, lfs, ps, pp, dd if depths is not None else None,
-                                                C.byref(o), _stream(stream)), "lfd_estimate_batch")
+        if warm is None:
+            self._check(self.lib.lfd_estimate_batch(self.h, n, lfs, ps, pp, dd if depths is not None else None,
+                                                    C.byref(o), _stream(stream)), "lfd_estimate_batch")
+            return planes, depths
+        assert len(warm) == n, "one warm entry per light field"
+        ww = (C.c_void_p * n)()
+        for l, (it, wp) in enumerate(zip(items, warm)):
+            if wp is None:
+                continue
+            wp = wp.contiguous()
+            V = len(it["K"])
+            S_l = [a * b for a, b in zip(*(([int(it[k])] * V if np.isscalar(it[k]) else [int(x) for x in it[k]])
+                                             for k in ("GW", "GH")))]
+            assert wp.is_cuda and wp.dtype == torch.float32 and wp.shape == (sum(S_l), 4)
+            offs = np.concatenate([[0], np.cumsum(S_l)[:-1]])
+            arr = _ptr_array([wp.data_ptr() + 16 * int(o_) for o_ in offs])
+            ww[l] = C.cast(arr, C.c_void_p)
+            keep += [arr, wp]
+        self._keep.append(ww)
+        self._check(self.lib.lfd_estimate_batch_warm(self.h, n, lfs, ps, ww, pp, dd if depths is not None else None,
+                                                     C.byref(o), _stream(stream)), "lfd_estimate_batch_warm")
         return planes, depths
 
     def fuse(self, depth_in, tau: float = 0.01, stream=None):
@@ -556,9 +585,9 @@ def terms_dict(rec: np.ndarray, nviews: int) -> dict:
 
 
 class Server:
-    """Frame server (lfd_server): rigs share one GPU through `max_slots`
-    context+stream slots; later frames of a rig start warm from its previous
-    planes."""
+    """Frame server (lfd_server): rigs share one GPU by continuous batching
+    over `max_slots` context+stream slots; later frames of a rig start warm
+    from its previous planes."""
 
     def __init__(self, device: int = 0, hbm_budget: int = 0, max_slots: int = 4):
         self.lib = load()
@@ -625,7 +654,15 @@ class Server:
         self._check(st, "lfd_server_poll")
         self._keep.pop(req_id, None)
         return dict(req_id=r.req_id, rig_id=r.rig_id, warm=r.warm, frame=r.frame, submit_ns=r.submit_ns,
-                    done_ns=r.done_ns, status=r.status, slot=r.slot)
+                    done_ns=r.done_ns, status=r.status, slot=r.slot, start_ns=r.start_ns, batch=r.batch)
+
+    def set_max_batch(self, n: int):
+        self._check(self.lib.lfd_server_set_max_batch(self.h, int(n)), "lfd_server_set_max_batch")
+
+    def stats(self) -> dict:
+        b, f = C.c_int64(), C.c_int64()
+        self._check(self.lib.lfd_server_stats(self.h, C.byref(b), C.byref(f)), "lfd_server_stats")
+        return {"batches": b.value, "frames": f.value}
 
     def export_state(self, rig_id: int) -> torch.Tensor:
         n = C.c_int64()

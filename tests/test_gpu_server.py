@@ -1,7 +1,8 @@
 """Serving form: the frame server gives each rig exactly what the plain calls
 give (cold frame = lfd_estimate; warm frame = lfd_estimate from the rig's
-previous planes with the warm schedule), whatever other rigs share the GPU;
-state moves between servers; budget and queue bounds are enforced."""
+previous planes with the warm schedule), whatever other rigs share the GPU
+and whichever batch a frame joins; a warm-started batch equals separate
+calls; state moves between servers; budget and queue bounds are enforced."""
 import pytest
 import torch
 
@@ -99,18 +100,65 @@ def test_rig_alone_equals_rig_in_a_mix(lfd, rigs):
     alone = _server(lfd, 1)
     a = _serve(lfd, alone, [(0, f) for f in range(3)], rigs)
     alone.close()
-    mix = _server(lfd, 3)
-    sched = []
-    for f in range(3):
-        for ri in (2, 0, 1):
-            sched.append((ri, f))
-    m = _serve(lfd, mix, sched, rigs)
-    slots = {m[(ri, 0)][0]["slot"] for ri in range(3)}
-    assert len(slots) == 3                                         # one slot per rig
-    for f in range(3):
-        assert torch.equal(a[(0, f)][1], m[(0, f)][1])
-        assert torch.equal(a[(0, f)][2], m[(0, f)][2])
-    mix.close()
+    for slots in (1, 2):
+        mix = _server(lfd, slots)
+        sched = []
+        for f in range(3):
+            for ri in (2, 0, 1):
+                sched.append((ri, f))
+        m = _serve(lfd, mix, sched, rigs)
+        # frames queued while others ran were merged into batches of several rigs
+        assert max(m[k][0]["batch"] for k in m) >= 2
+        assert all(m[k][0]["start_ns"] >= m[k][0]["submit_ns"] for k in m)
+        st = mix.stats()
+        assert st["frames"] == len(sched) and st["batches"] < len(sched)
+        for f in range(3):
+            assert torch.equal(a[(0, f)][1], m[(0, f)][1])
+            assert torch.equal(a[(0, f)][2], m[(0, f)][2])
+        mix.close()
+
+
+def test_max_batch_one_runs_frames_alone(lfd, rigs):
+    srv = _server(lfd, 1)
+    srv.set_max_batch(1)
+    m = _serve(lfd, srv, [(ri, 0) for ri in range(3)] + [(ri, 1) for ri in range(3)], rigs)
+    assert all(v[0]["batch"] == 1 for v in m.values())
+    srv.close()
+
+
+def test_warm_batch_equals_separate_calls(lfd, rigs):
+    """lfd_estimate_batch_warm with a cold light field between two warm ones
+    (the sweep leaves the warm views out) gives the separate calls' bits."""
+    prev = []
+    for r in rigs:
+        ref = _reference(lfd, r, 1)
+        prev.append(ref[0][0])
+    ctx = lfd.Context(0)
+    items, warm, expect = [], [], []
+    for ri, r in enumerate(rigs):
+        fr = _frame(r, 1)
+        p = dict(r.params)
+        w = None
+        if ri != 1:
+            p.update(iterations=3, warm_iter_offset=3)
+            w = prev[ri]
+        items.append(dict(views=fr["views"], labels=fr["labels"], K=fr["K"], R=fr["R"], t=fr["t"], GW=fr["GW"],
+                          GH=fr["GH"], params=p))
+        warm.append(w)
+        c1 = lfd.Context(0)
+        pl, dp = c1.estimate(fr["views"], fr["labels"], fr["K"], fr["R"], fr["t"], fr["GW"], fr["GH"], p, warm=w)
+        c1.synchronize()
+        expect.append((pl.clone(), dp.clone()))
+        c1.close()
+    planes, depths = ctx.estimate_batch(items, warm=warm)
+    ctx.synchronize()
+    base = 0
+    for ri, r in enumerate(rigs):
+        S = r.V * r.GW * r.GH
+        assert torch.equal(planes[base:base + S], expect[ri][0])
+        assert torch.equal(depths[ri], expect[ri][1])
+        base += S
+    ctx.close()
 
 
 def test_state_export_import_continues_the_stream(lfd, rigs):
