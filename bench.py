@@ -3,16 +3,25 @@
 
 One step = one whole frame through lfd_estimate: superpixel build, plane
 sweep, every refinement iteration and the final depth rasterisation, on a
-synthetic camera-array scene shaped like the paper's workloads.  The headline
-metric is plane-hypothesis evaluations per second (a (superpixel, candidate
-plane) scoring over all its pixels and neighbour views); ms per view and
-pixel-view samples per second are reported beside it.
+synthetic camera-array scene shaped like the paper's workloads.  The default
+run measures, in one JSON line:
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 2] [--impl ours|reference]
+  * the headline: 16 views 1920x1080 FP16 (8160 superpixels per view, 256
+    labels, 8 iterations): plane-hypothesis evaluations per second (a
+    (superpixel, candidate plane) scoring over all its pixels and neighbour
+    views) and ms per 1080p view, with the roofline of the dominant kernel,
+    the FP64 oracle timed on the host cores on a superpixel sample, and the
+    same frame end to end from pinned host memory;
+  * "config2": the same measurement on 8 views 1024x768 RGBA8;
+  * "serving": three rigs streaming frames into the frame server, p50/p99
+    latency per rig at the offered 30 fps per rig and at 0.8 x capacity.
 
-N > 1 runs under torch.distributed.run: independent replicas (the hot path has
-no exchange step at one light field per GPU), value = all ranks' evaluations
-divided by the slowest rank's time.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1|2|3|4] [--serve] [--impl ours|reference]
+
+--config N measures that configuration alone (4: the batched mix); --serve
+prints the serving line alone.  N > 1 runs under torch.distributed.run:
+independent replicas (one light field per GPU has no exchange step), value =
+all ranks' evaluations divided by the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -35,14 +44,21 @@ import torch  # noqa: E402
 
 METRIC = "plane-hypothesis evals/s"
 UNIT = "evals/s"
+HEADLINE_CONFIG = 3
 L2_FLUSH_BYTES = 256 << 20
-# algorithmic FP32 operations per pixel-view sample, counted from the method's
-# arithmetic (address arithmetic excluded): sweep = projection 15, floor and
-# fraction 2, bilinear 19, SSD 8, truncation and accumulation 2; propagation =
-# projection 12, reciprocal 1, division 2, rounding 2, Eq. 9 weight 8, X/Y
-# test 2, Eq. 10 Gaussian 4, accumulation 4
-FLOPS_PER_SAMPLE = {"sweep": 46, "propagate": 35}
-SM_COUNT_GB300 = 152
+# Algorithmic work per pixel-view sample of the two hot kernels.
+# Gathered bytes (the level that bounds a gather-heavy kernel): the sweep's
+# bilinear sample reads a 2x2 block of source texels (4 texels of 4 B for
+# RGBA8, 8 B for FP16/BF16, 16 B for FP32; neighbouring samples share them),
+# the energy sample one rasterised texel {superpixel label, depth} of 8 B (the
+# superpixel colours are a small table that stays in L1).
+# FP32 operations: sweep ~40 (homography column 3, reciprocal 1, floor and
+# fraction 4, bilinear 3 x 3 FMA + weight 1, SSD 3 + 3, truncation and
+# accumulation 2 ...), energy ~17 (projection 6 + 2, reciprocal 1, Eq. 9 colour
+# distance 5 and weight, Eq. 10 Gaussian, accumulation), one of each counted
+# as one operation.
+GATHER_BYTES_PER_SAMPLE = {"sweep": {0: 16, 1: 32, 2: 32, 3: 64}, "propagate": {0: 8, 1: 8, 2: 8, 3: 8}}
+OPS_PER_SAMPLE = {"sweep": 40, "propagate": 17}
 FP32_LANES_PER_SM = 128
 
 
@@ -103,17 +119,41 @@ def l2_copy_peak_gbs(dev) -> float:
     return 2 * a.numel() * 4 / (best / 1000.0) / 1e9
 
 
-def level_rates(kernel: str, wkey: str, avg_launch_ms: float, dev) -> dict:
-    """Memory-level view of the dominant kernel beside its FP32 roofline:
-    DRAM and L2 bytes per launch from the recorded ncu capture over the live
-    launch time, against the measured HBM copy peak and an L2 copy peak
-    measured here."""
-    dram = recorded_traffic(kernel, wkey, 2)
-    l2 = recorded_traffic(kernel, wkey, 4)
+def roofline_of(kernel: str, fmt: int, samples_per_launch: float, avg_launch_ms: float, dev, wkey: str,
+                l2_peak_gbs: float) -> dict:
+    """Roofline of the dominant kernel at the level that bounds a gather
+    kernel: algorithmic gathered bytes per launch (samples x bytes per
+    sample) over the live launch time, against an L2-resident copy measured
+    in this run.  Beside it the FP32 view (operations per sample over the
+    FP32 lane peak of this device at its maximum clock) and the recorded DRAM
+    traffic of the same launch (ncu)."""
+    props = torch.cuda.get_device_properties(dev)
+    sms = int(props.multi_processor_count)
     sec = avg_launch_ms / 1000.0
-    return {"hbm_peak_gbs": measured_peaks().get("hbm_gbs"), "l2_copy_peak_gbs": l2_copy_peak_gbs(dev),
-            "dram_gbs": dram / sec / 1e9 if dram else None, "l2_gbs": l2 / sec / 1e9 if l2 else None,
-            "note": "bytes per launch from profiles/dram_traffic.txt (ncu), time from this run's CUDA events"}
+    gbytes = GATHER_BYTES_PER_SAMPLE[kernel][fmt] * samples_per_launch
+    achieved = gbytes / sec / 1e9
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    ops = OPS_PER_SAMPLE[kernel] * samples_per_launch
+    dram = recorded_traffic(f"k_{kernel}", wkey, 2)
+    l2 = recorded_traffic(f"k_{kernel}", wkey, 4)
+    return {"bound": "l2", "kernel": f"k_{kernel}", "achieved": achieved, "peak": l2_peak_gbs, "unit": "GB/s",
+            "frac": achieved / l2_peak_gbs, "traffic": dram,
+            "traffic_unit": "DRAM bytes per launch (ncu capture of this workload, profiles/dram_traffic.txt; "
+                            "null when the kernel's sources changed since)",
+            "algorithmic": f"{GATHER_BYTES_PER_SAMPLE[kernel][fmt]} B gathered per pixel-view sample x "
+                           f"{samples_per_launch:.4g} samples per launch",
+            "peak_note": "L2-resident copy (read + write bytes), measured in this run",
+            "avg_launch_ms": avg_launch_ms,
+            "fp32": {"achieved_tflops": ops / sec / 1e12, "peak_tflops": fp32_peak,
+                     "frac": ops / sec / 1e12 / fp32_peak,
+                     "note": f"{OPS_PER_SAMPLE[kernel]} FP32 operations per sample; peak = {sms} SMs x "
+                             f"{FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz"},
+            "levels": {"hbm_peak_gbs": peaks.get("hbm_gbs"),
+                       "dram_gbs": dram / sec / 1e9 if dram else None,
+                       "l2_gbs_measured": l2 / sec / 1e9 if l2 else None,
+                       "l2_bytes_over_algorithmic": l2 / gbytes if l2 else None}}
 
 
 def workload_name(cfg: int, lf) -> str:
@@ -218,6 +258,12 @@ def build_inputs(cfg: int, device: str, scale: float = 1.0):
     return lf, views, labels, params
 
 
+# superpixel fraction of each configuration that the oracle scores for the
+# CPU baseline (about 10 s of host work) and per reference step
+CPU_SAMPLE = {1: 1.0, 2: 0.25, 3: 0.03}
+REF_SAMPLE = {1: 0.2, 2: 0.004, 3: 0.004}
+
+
 def oracle_views_rgb(views):
     from paper_1812_06856_gb300 import synth
     v = views.cpu()
@@ -256,27 +302,30 @@ def host_cores():
 
 def run_reference(args):
     """--impl reference: the oracle as it stands on the host cores, on a bounded
-    superpixel sample of the same workload per step."""
+    superpixel sample of the same workload per step.  The synthetic inputs are
+    rendered on the GPU when there is one (input generation only)."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     from paper_1812_06856_gb300 import synth
-    if args.config == 4:         # sampled from light field 0 of the batch
-        m0 = synth.make_mix(1, "cpu", scale=args.scale)[0]
-        views, params = m0.views, m0.params
-        lf = synth.LightField("mix-0", m0.rig, None, oracle_views_rgb(views), None, None, m0.labels.numpy(),
+    cfg = args.config or HEADLINE_CONFIG
+    gen_dev = f"cuda:{local}" if torch.cuda.is_available() else "cpu"
+    if cfg == 4:                 # sampled from light field 0 of the batch
+        m0 = synth.make_mix(1, gen_dev, scale=args.scale)[0]
+        views, params = m0.views.cpu(), m0.params
+        lf = synth.LightField("mix-0", m0.rig, None, oracle_views_rgb(views), None, None, m0.labels.cpu().numpy(),
                               m0.GW, m0.GH, m0.params, m0.pitch)
     else:
-        lf = synth.make_config(args.config, device="cpu")
-        if args.config == 3:
-            views = synth.to_rgba_float(lf.rgb, torch.float16)
-        else:
-            views = synth.quantize_rgba8(lf.rgb)
-        params = synth.method_params(lf)
+        lf, views, _, params = build_inputs(cfg, gen_dev, args.scale)
+        views = views.cpu()
+        lf.labels = np.asarray(lf.labels.cpu() if hasattr(lf.labels, "cpu") else lf.labels)
+        if gen_dev != "cpu":
+            torch.cuda.synchronize()
     cores = host_cores()
     o = make_oracle(lf, views, params, cores)
     rng = np.random.default_rng(99)
-    n = max(cores, int(round(args.ref_sample * o.S_total)))
+    frac = args.ref_sample if args.ref_sample is not None else REF_SAMPLE.get(cfg, 0.004)
+    n = max(cores, int(round(frac * o.S_total)))
     times, hyps = [], []
     for step in range(args.warmup + args.steps):
         items = np.sort(rng.choice(o.S_total, size=n, replace=False)).astype(np.int32)
@@ -290,30 +339,29 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": mix_workload_name(args.mix, args.scale) if args.config == 4
-                       else workload_name(args.config, lf), "sample": sample},
+            "config": {"workload": mix_workload_name(args.mix, args.scale) if cfg == 4
+                       else workload_name(cfg, lf), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0, "roofline": None, "clocks": None}     # host cores only
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = f"cuda:{local}"
+def measure_frames(cfg: int, args, dev: str, local: int, ws: int, l2_peak: float, flush, extras: bool) -> tuple:
+    """Time args.steps frames of configuration cfg through lfd_estimate
+    (device-resident inputs, L2 flushed between frames), the roofline of the
+    dominant kernel, and (unless --no-e2e) the same frames end to end through
+    lfd_estimate_host from pinned host memory.  extras: also time the depth
+    fusion and the GPU SLIC on the frame.  Returns (result dict, light field,
+    views, params)."""
     from paper_1812_06856_gb300 import lfd
-    lf, views, labels, params = build_inputs(args.config, dev, args.scale)
+    lf, views, labels, params = build_inputs(cfg, dev, args.scale)
     V, H, W = lf.rig.V, lf.rig.H, lf.rig.W
     ctx = lfd.Context(local)
     K, R, t, GW, GH = lf.rig.K, lf.rig.R, lf.rig.t, lf.GW, lf.GH
     S_total = V * GW * GH
     planes = torch.zeros((S_total, 4), dtype=torch.float32, device=dev)
     depth = torch.zeros((V, H, W), dtype=torch.float32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -364,65 +412,44 @@ def run_ours(args):
     dom = max(("sweep", "propagate"), key=lambda k: stage_ms[k])
     dom_samples = sweep_samples if dom == "sweep" else prop_samples
     launches = max(stage_launches[dom], 1)
-    avg_launch_ms = stage_ms[dom] / launches
-    flops_per_launch = FLOPS_PER_SAMPLE[dom] * dom_samples / launches
-    achieved = flops_per_launch / (avg_launch_ms / 1000.0) / 1e12
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    wkey = f"config{args.config}@{args.scale:g}"
-    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(f"k_{dom}", wkey),
-                "traffic_unit": "DRAM bytes per launch (ncu, profiles/dram_traffic.txt)",
-                "peak_note": f"FP32 FMA peak {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
-                             f"{sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
-                "algorithmic": f"{FLOPS_PER_SAMPLE[dom]} FP32 flop per pixel-view sample x "
-                               f"{dom_samples / launches:.4g} samples per launch",
-                "avg_launch_ms": avg_launch_ms, "levels": level_rates(f"k_{dom}", wkey, avg_launch_ms, dev)}
+    fmt = 1 if cfg == 3 else 0
+    roofline = roofline_of(dom, fmt, dom_samples / launches, stage_ms[dom] / launches, dev,
+                           f"config{cfg}@{args.scale:g}", l2_peak)
+    res = {"workload": workload_name(cfg, lf), "value": value, "ms_per_step": ms, "ms_per_view": ms / V,
+           "samples_per_s": samples_per_s, "hypotheses_per_step": hyp_step, "samples_per_step": samples_step,
+           "stage_ms": stage_ms, "wall_s": wall, "gpu_launches": int(sum(v[1] for v in prof.values())),
+           "roofline": roofline, "clocks": clock_info}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(args.config, lf), "l2": "flushed between steps (256 MiB write)",
-                       "inputs": "device-resident", "parallelism": f"replicas x{ws}"},
-            "ms_per_view": ms / V, "samples_per_s": samples_per_s,
-            "hypotheses_per_step": hyp_step, "samples_per_step": samples_step,
-            "stage_ms": stage_ms, "wall_s": wall,
-            "gpu_launches": int(sum(v[1] for v in prof.values())),
-            "roofline": roofline, "clocks": clock_info}
-
-    # stability-based fusion (Section III-D) of the frame's depth maps: not part
-    # of the timed frame step (the step is the hot path a1-a8); timed beside it
-    fused = None
-    for _ in range(2):
-        fused = ctx.fuse(depth)
-    fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
-    for a, b in fev:
-        flush.fill_(3)
-        a.record(stream)
-        ctx.fuse(depth)
-        b.record(stream)
-    torch.cuda.synchronize()
-    f_ms = float(np.mean([a.elapsed_time(b) for a, b in fev]))
-    line["fusion"] = {"ms": f_ms, "ms_per_view": f_ms / V, "tau": 0.01,
-                      "changed_fraction": float((fused != depth).float().mean().item())}
-    del fused
-
-    # GPU SLIC (the segmentation before Section III-A) of the frame's views,
-    # 10 iterations, one superpixel per grid cell of the frame: timed beside
-    # the step like the fusion
-    for _ in range(2):
-        ctx.slic(views, lf.GW, lf.GH, 10.0, iterations=10, stream=stream)
-    sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
-    for a, b in sev:
-        flush.fill_(3)
-        a.record(stream)
-        ctx.slic(views, lf.GW, lf.GH, 10.0, iterations=10, stream=stream)
-        b.record(stream)
-    torch.cuda.synchronize()
-    s_ms = float(np.mean([a.elapsed_time(b) for a, b in sev]))
-    line["slic"] = {"ms": s_ms, "ms_per_view": s_ms / V, "iterations": 10, "compactness": 10.0,
-                    "cells": [int(lf.GW), int(lf.GH)]}
+    if extras:
+        # stability-based fusion (Section III-D) of the frame's depth maps and the
+        # GPU SLIC (the segmentation before Section III-A): not part of the timed
+        # frame step (the step is the hot path a1-a8); timed beside it
+        fused = None
+        for _ in range(2):
+            fused = ctx.fuse(depth)
+        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        for a, b in fev:
+            flush.fill_(3)
+            a.record(stream)
+            ctx.fuse(depth)
+            b.record(stream)
+        torch.cuda.synchronize()
+        f_ms = float(np.mean([a.elapsed_time(b) for a, b in fev]))
+        res["fusion"] = {"ms": f_ms, "ms_per_view": f_ms / V, "tau": 0.01,
+                         "changed_fraction": float((fused != depth).float().mean().item())}
+        del fused
+        for _ in range(2):
+            ctx.slic(views, lf.GW, lf.GH, 10.0, iterations=10, stream=stream)
+        sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        for a, b in sev:
+            flush.fill_(3)
+            a.record(stream)
+            ctx.slic(views, lf.GW, lf.GH, 10.0, iterations=10, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        s_ms = float(np.mean([a.elapsed_time(b) for a, b in sev]))
+        res["slic"] = {"ms": s_ms, "ms_per_view": s_ms / V, "iterations": 10, "compactness": 10.0,
+                       "cells": [int(lf.GW), int(lf.GH)]}
 
     # end to end through the host-memory entry point
     if not args.no_e2e:
@@ -443,24 +470,68 @@ def run_ours(args):
             evs[k][1].record(stream)
         barrier()
         e_ms, e_value = replica_reduce(float(np.mean([a.elapsed_time(b) for a, b in evs])), hyp_step, ws, dev)
-        line["e2e"] = {"value": e_value, "unit": UNIT,
-                       "h2d_bytes_per_step": int(vh.numel() * vh.element_size() + lh.numel() * 4),
-                       "d2h_bytes_per_step": int(ph.numel() * 4 + dh.numel() * 4), "ms_per_step": e_ms}
+        res["e2e"] = {"value": e_value, "unit": UNIT,
+                      "h2d_bytes_per_step": int(vh.numel() * vh.element_size() + lh.numel() * 4),
+                      "d2h_bytes_per_step": int(ph.numel() * 4 + dh.numel() * 4), "ms_per_step": e_ms,
+                      "ms_per_view": e_ms / V}
         ctx_h.close()
+        del vh, lh, ph, dh
+    ctx.close()
+    del planes, depth, labels
+    return res, lf, views, params
 
+
+def cpu_baseline_of(cfg: int, lf, views, params, frac: float) -> dict:
+    """The oracle as it stands on the host cores (all threads), on a
+    deterministic superpixel sample of the same workload: the sample's sweep
+    and its refinement iteration 1."""
+    cores = host_cores()
+    o = make_oracle(lf, views, params, cores)
+    rng = np.random.default_rng(1234)
+    n = max(cores, int(round(frac * o.S_total)))
+    items = np.sort(rng.choice(o.S_total, size=n, replace=False)).astype(np.int32)
+    h, dt = oracle_sample_step(o, params, items)
+    return {"value": h / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"config {cfg}: {n} of {o.S_total} superpixels (deterministic random sample): their sweep "
+                      f"and refinement iteration 1, {h} hypotheses in {dt:.1f} s, FP64 oracle"}
+
+
+def run_ours(args):
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    l2_peak = l2_copy_peak_gbs(dev)
+    cfg = args.config or HEADLINE_CONFIG
+    head, lf, views, params = measure_frames(cfg, args, dev, local, ws, l2_peak, flush, extras=True)
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": head["workload"], "l2": "flushed between steps (256 MiB write)",
+                       "inputs": "device-resident", "parallelism": f"replicas x{ws}",
+                       "storage": "FP16 views, FP32 accumulation" if cfg == 3 else "RGBA8 views, FP32 accumulation"},
+            "ms_per_view": head["ms_per_view"]}
+    for k in ("samples_per_s", "hypotheses_per_step", "samples_per_step", "stage_ms", "wall_s", "gpu_launches",
+              "roofline", "clocks", "fusion", "slic", "e2e"):
+        if k in head:
+            line[k] = head[k]
     if rank == 0 and not args.no_cpu_baseline:
-        cores = host_cores()
-        o = make_oracle(lf, views, params, cores)
-        rng = np.random.default_rng(1234)
-        n = max(cores, int(round(args.cpu_sample * o.S_total)))
-        items = np.sort(rng.choice(o.S_total, size=n, replace=False)).astype(np.int32)
-        h, dt = oracle_sample_step(o, params, items)
-        line["cpu_baseline"] = {"value": h / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{n} of {o.S_total} superpixels (deterministic random sample): their sweep "
-                                          f"and refinement iteration 1, {h} hypotheses in {dt:.1f} s, FP64 oracle"}
+        frac = args.cpu_sample if args.cpu_sample is not None else CPU_SAMPLE.get(cfg, 0.05)
+        line["cpu_baseline"] = cpu_baseline_of(cfg, lf, views, params, frac)
+    del views
+    if args.config is None:
+        # the 8 x 1024x768 configuration in a block of its own
+        c2, _, _, _ = measure_frames(2, args, dev, local, ws, l2_peak, flush, extras=False)
+        line["config2"] = {k: c2[k] for k in ("workload", "value", "ms_per_step", "ms_per_view", "samples_per_s",
+                                              "hypotheses_per_step", "stage_ms", "gpu_launches", "roofline",
+                                              "clocks", "e2e") if k in c2}
+        if ws == 1 and not args.no_serve:
+            line["serving"] = serving_block(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -534,19 +605,8 @@ def run_ours_batch(args):
     dom = max(("sweep", "propagate"), key=lambda k: stage_ms[k])
     dom_samples = sweep_samples if dom == "sweep" else prop_samples
     launches = max(stage_launches[dom], 1)
-    avg_launch_ms = stage_ms[dom] / launches
-    achieved = FLOPS_PER_SAMPLE[dom] * dom_samples / launches / (avg_launch_ms / 1000.0) / 1e12
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(f"k_{dom}", f"config4@{args.scale:g}"),
-                "traffic_unit": "DRAM bytes per launch (ncu, profiles/dram_traffic.txt)",
-                "peak_note": f"FP32 FMA peak {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
-                             f"{sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
-                "algorithmic": f"{FLOPS_PER_SAMPLE[dom]} FP32 flop per pixel-view sample x "
-                               f"{dom_samples / launches:.4g} samples per launch",
-                "avg_launch_ms": avg_launch_ms}
+    roofline = roofline_of(dom, 0, dom_samples / launches, stage_ms[dom] / launches, dev,
+                           f"config4@{args.scale:g}", l2_copy_peak_gbs(dev))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -617,22 +677,25 @@ def _percentile(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if xs else None
 
 
-def run_serving(args):
+def serving_block(args) -> dict:
     """Serving workload: rigs A (8 x 1024x768 arc), B (9 x 1280x720 3x3 grid)
-    and C (16 x 1920x1080 4x4 grid), each moving <= 2 cm per frame, frames
-    arriving as a Poisson process of --serve-fps per rig into one frame
-    server (one slot per rig, warm start: 3 iterations at I = 4..6, at most
-    --serve-pending frames of a rig in flight; a frame arriving beyond that
-    is dropped).  Latency = arrival -> depth maps ready (host monotonic clock,
-    set by a stream callback at the end of the frame)."""
-    torch.cuda.set_device(0)
+    and C (16 x 1920x1080 4x4 grid), each moving <= 2 cm per frame, into one
+    frame server doing continuous batching over --serve-slots slots (warm
+    start: 3 iterations at I = 4..6; at most --serve-pending frames of a rig
+    submitted and not yet done: a frame arriving beyond that is dropped).
+    Measured: each rig's frames alone, the closed-loop capacity of the three
+    rigs batched, and Poisson arrivals at --serve-fps per rig and at 0.8 x the
+    batched capacity.  Latency = arrival -> depth maps ready (host monotonic
+    clock, set by a stream callback at the end of the frame's batch), split
+    into queueing (arrival -> batch launch) and service (launch -> ready)."""
     from paper_1812_06856_gb300 import lfd
     from paper_1812_06856_gb300 import synth
     t_gen = time.perf_counter()
     rigs = [synth.make_serving_rig(n, "cuda", keyframes=args.serve_keyframes, scale=args.scale)
             for n in synth.SERVING_RIGS]
+    torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    srv = lfd.Server(0, 64 << 30, len(rigs))
+    srv = lfd.Server(torch.cuda.current_device(), 64 << 30, args.serve_slots)
     srv.configure(3, 3, args.serve_pending)
     ring = args.serve_pending + 1
     outs = []
@@ -654,14 +717,39 @@ def run_serving(args):
 
     # each rig alone: cold frame, then warm frames one at a time
     alone = {}
+    frame_no = [0] * len(rigs)
     for ri, r in enumerate(rigs):
         cold = srv.poll(submit(ri, 0), -1)
         warm = []
         for f in range(1, 6):
             res = srv.poll(submit(ri, f), -1)
             warm.append((res["done_ns"] - res["submit_ns"]) / 1e6)
+        frame_no[ri] = 6
         alone[r.name] = {"cold_ms": (cold["done_ns"] - cold["submit_ns"]) / 1e6, "warm_ms": float(np.median(warm))}
-    busy_s = sum(alone[r.name]["warm_ms"] for r in rigs) / 1000.0      # GPU seconds per frame of every rig
+    busy_s = sum(alone[r.name]["warm_ms"] for r in rigs) / 1000.0      # GPU seconds per frame of every rig, alone
+
+    # closed loop: every rig submits its next frame as soon as its previous one is done
+    rounds = 20
+    b0 = srv.stats()
+    t0 = time.perf_counter()
+    live = {ri: submit(ri, frame_no[ri]) for ri in range(len(rigs))}
+    done_frames = [0] * len(rigs)
+    while any(d < rounds for d in done_frames):
+        for ri in range(len(rigs)):
+            if live.get(ri) is None:
+                continue
+            res = srv.poll(live[ri], 0)
+            if res is None:
+                continue
+            done_frames[ri] += 1
+            frame_no[ri] += 1
+            live[ri] = submit(ri, frame_no[ri]) if done_frames[ri] < rounds else None
+        time.sleep(0.0001)
+    closed_s = time.perf_counter() - t0
+    b1 = srv.stats()
+    capacity = rounds / closed_s
+    closed = {"rounds": rounds, "seconds": closed_s, "capacity_fps_per_rig": capacity,
+              "mean_batch": (b1["frames"] - b0["frames"]) / max(1, b1["batches"] - b0["batches"])}
 
     def poisson_run(fps, duration_s, seed):
         rng = np.random.default_rng(seed)
@@ -670,17 +758,22 @@ def run_serving(args):
             t = np.cumsum(rng.exponential(1.0 / fps, size=int(duration_s * fps * 1.5) + 8))
             events += [(float(x), ri) for x in t[t < duration_s]]
         events.sort()
-        frame_no = [1000] * len(rigs)
         lat = {r.name: [] for r in rigs}
+        wait = {r.name: [] for r in rigs}
+        serv = {r.name: [] for r in rigs}
         dropped = {r.name: 0 for r in rigs}
         outstanding = {}
+        s0 = srv.stats()
 
         def drain(timeout_us):
             for rid in list(outstanding):
                 res = srv.poll(rid, timeout_us)
                 if res is not None:
                     ri, arr = outstanding.pop(rid)
-                    lat[rigs[ri].name].append((res["done_ns"] - arr) / 1e6)
+                    nm = rigs[ri].name
+                    lat[nm].append((res["done_ns"] - arr) / 1e6)
+                    wait[nm].append((res["start_ns"] - arr) / 1e6)
+                    serv[nm].append((res["done_ns"] - res["start_ns"]) / 1e6)
 
         t0 = lfd.Server.now_ns() + 20_000_000
         for ta, ri in events:
@@ -697,53 +790,76 @@ def run_serving(args):
                 outstanding[rid] = (ri, arr)
         drain(-1)
         wall = (lfd.Server.now_ns() - t0) / 1e9
+        s1 = srv.stats()
         per = {}
         for r in rigs:
             xs = lat[r.name]
             per[r.name] = {"p50_ms": _percentile(xs, 50), "p99_ms": _percentile(xs, 99),
                            "mean_ms": float(np.mean(xs)) if xs else None, "served": len(xs),
-                           "dropped": dropped[r.name], "served_fps": len(xs) / wall}
-        return {"fps_per_rig": fps, "duration_s": duration_s, "offered_over_capacity": fps * busy_s, "rigs": per,
+                           "dropped": dropped[r.name], "served_fps": len(xs) / wall,
+                           "queue_p50_ms": _percentile(wait[r.name], 50), "queue_p99_ms": _percentile(wait[r.name], 99),
+                           "service_p50_ms": _percentile(serv[r.name], 50),
+                           "service_p99_ms": _percentile(serv[r.name], 99)}
+        return {"fps_per_rig": fps, "duration_s": duration_s, "offered_over_capacity": fps / capacity, "rigs": per,
+                "mean_batch": (s1["frames"] - s0["frames"]) / max(1, s1["batches"] - s0["batches"]),
                 "p99_worst_ms": max(v["p99_ms"] for v in per.values() if v["p99_ms"] is not None)}
 
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     nominal = poisson_run(args.serve_fps, args.serve_seconds, 1812)
-    fps_ok = 0.8 / busy_s
-    sustainable = poisson_run(fps_ok, args.serve_seconds, 1813)
+    sustainable = poisson_run(0.8 * capacity, args.serve_seconds, 1813)
     clock_info = clocks.stop()
-    line = {"metric": "serving p99 frame latency (worst rig)", "value": sustainable["p99_worst_ms"], "unit": "ms",
-            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving: rigs A 8x1024x768 arc, B 9x1280x720 3x3 grid, C 16x1920x1080 4x4 grid, "
-                                   f"moving 1.5 cm/frame, {args.serve_keyframes} rendered keyframes walked back and "
-                                   "forth, Poisson arrivals per rig, warm start 3 iterations at I = 4..6",
-                       "scale": args.scale, "slots": len(rigs), "max_pending_per_rig": args.serve_pending},
-            "value_note": "p99 of the worst rig at 0.8 x capacity (capacity = rigs' warm-frame times alone, summed)",
-            "alone": alone, "capacity_fps_per_rig": 1.0 / busy_s,
+    srv.close()
+    return {"workload": "serving: rigs A 8x1024x768 arc, B 9x1280x720 3x3 grid, C 16x1920x1080 4x4 grid, "
+                        f"moving 1.5 cm/frame, {args.serve_keyframes} rendered keyframes walked back and forth, "
+                        "Poisson arrivals per rig, warm start 3 iterations at I = 4..6, continuous batching",
+            "scale": args.scale, "slots": args.serve_slots, "max_pending_per_rig": args.serve_pending,
+            "p99_worst_ms_at_0p8_capacity": sustainable["p99_worst_ms"],
+            "alone": alone, "capacity_fps_per_rig_alone_sum": 1.0 / busy_s,
+            "closed_loop_batched": closed, "capacity_fps_per_rig": capacity,
             "nominal": nominal, "at_0p8_capacity": sustainable, "clocks": clock_info,
             "input_generation_s": t_gen}
+
+
+def run_serving(args):
+    """--serve: the serving workload alone, its own JSON line (value = p99
+    latency of the worst rig at 0.8 x capacity)."""
+    torch.cuda.set_device(0)
+    blk = serving_block(args)
+    line = {"metric": "serving p99 frame latency (worst rig)", "value": blk["p99_worst_ms_at_0p8_capacity"],
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": blk["workload"], "scale": blk["scale"], "slots": blk["slots"],
+                       "max_pending_per_rig": blk["max_pending_per_rig"]},
+            "value_note": "p99 of the worst rig at 0.8 x the closed-loop batched capacity"}
+    line.update({k: blk[k] for k in ("alone", "capacity_fps_per_rig_alone_sum", "closed_loop_batched",
+                                     "capacity_fps_per_rig", "nominal", "at_0p8_capacity", "clocks",
+                                     "input_generation_s")})
     print(json.dumps(line), flush=True)
-    srv.close()
+
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
-                    help="1-3: one light field per step; 4: the batched mix of --mix light fields")
+    ap.add_argument("--config", type=int, default=None, choices=[1, 2, 3, 4],
+                    help="measure one configuration alone (1-3: one light field per step; 4: the batched mix of "
+                         "--mix light fields); default: the 16 x 1080p headline with config-2 and serving blocks")
     ap.add_argument("--mix", type=int, default=64, help="light fields of config 4")
     ap.add_argument("--scale", type=float, default=1.0, help="resolution scale (small cases for profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=float, default=0.25, help="superpixel fraction timed on the CPU oracle")
-    ap.add_argument("--ref-sample", type=float, default=0.004, help="superpixel fraction per reference step")
+    ap.add_argument("--cpu-sample", type=float, default=None,
+                    help="superpixel fraction timed on the CPU oracle (default per configuration, ~10 s)")
+    ap.add_argument("--ref-sample", type=float, default=None, help="superpixel fraction per reference step")
+    ap.add_argument("--no-serve", action="store_true", help="leave the serving block out of the default run")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead (its own JSON line)")
     ap.add_argument("--serve-fps", type=float, default=30.0, help="offered frames/s per rig (nominal run)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window of each serving run")
     ap.add_argument("--serve-keyframes", type=int, default=4)
     ap.add_argument("--serve-pending", type=int, default=2, help="frames of a rig in flight before drops")
+    ap.add_argument("--serve-slots", type=int, default=2, help="frame-server slots (batches in flight at once)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("note: timing rules ask for at least 3 warm-up steps", file=sys.stderr)
