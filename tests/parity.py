@@ -21,8 +21,29 @@ from oracle import oracle as orc
 from paper_1812_06856_gb300 import synth
 
 REL = 1e-4      # per-hypothesis relative tolerance of the path's floating-point terms
-ABS = 1e-6      # absolute floor for terms of O(1) magnitude computed with FP32 exp/rcp
+ABS = 1e-7      # absolute floor (terms near 0: V_i, O_i, a Gaussian far in its tail)
+# Two candidates whose energies each carry an error up to REL can swap when
+# their gap is below 2 REL; a GPU choice is an admissible tie when its upper
+# bound reaches the best lower bound within that, plus 25 %.
 TIE_REL = 2.5e-4
+# Absolute floor of a truncated-SSD sum (Eq. 2), per pixel-view sample: the
+# bilinear colour an FP32 implementation interpolates is within ~3 ulp of 1
+# (1.8e-7 in [0,1] units) of the exact value, so an untruncated SSD, whose
+# colour differences sum to at most sqrt(3 T) = 0.35, moves by at most
+# 2 * 0.35 * 1.8e-7 = 1.3e-7.  A sum of costs that nearly match (a cost far
+# below 1e-3 per sample) is bounded by this, not by REL.
+TSSD_ABS_PER_SAMPLE = 1.3e-7
+
+
+def tssd_abs_floor(o, items=None) -> np.ndarray:
+    """Per superpixel (global index, or `items`): TSSD_ABS_PER_SAMPLE x its
+    pixel-view samples (pixels x neighbour views)."""
+    out = []
+    for v in range(o.V):
+        cnt = o.sp_stats(v)["cnt"].astype(np.float64)
+        out.append(cnt * len(o.neighbor_views(v)) * TSSD_ABS_PER_SAMPLE)
+    f = np.concatenate(out)
+    return f if items is None else f[np.asarray(items)]
 
 
 def gpu_inputs(lf: synth.LightField, fmt: str = "rgba8", device="cuda"):

@@ -91,7 +91,8 @@ def _sweep_compare(lfd, lf, views, labels, params, o, report):
     planes, lab, costs = planes.cpu().numpy(), lab.cpu().numpy(), costs.cpu().numpy().astype(np.float64)
     sw = o.sweep(np.arange(o.S_total), want_costs=True)
     ne = sw["label"] >= 0
-    ok = PT.within(costs[ne], sw["cost_lo"][ne], sw["cost_hi"][ne])
+    floor = PT.tssd_abs_floor(o)[:, None] + PT.ABS
+    ok = PT.within(costs[ne], sw["cost_lo"][ne], sw["cost_hi"][ne], absf=floor[ne])
     unfl = sw["cost_lo"][ne] == sw["cost_hi"][ne]
     err = PT.rel_err(costs[ne][unfl], sw["cost"][ne][unfl])
     same = lab == sw["label"]
@@ -312,6 +313,7 @@ def test_iterations_state_injected_config1(lfd, cfg1):
         print(f"iteration {it} state-injected:", rep)
         assert adm.all()
         assert rep["identical_when_decided"] == 1.0
+        assert rep["depth_within_0p5pct"] == 1.0
         state = out
 
 
@@ -330,8 +332,44 @@ def test_iterations_state_injected_with_split_tolerance(lfd):
         rep = {}
         out, same, adm = _iterate_compare(lfd, ctx, o, state, it, items, rep)
         print(f"iteration {it} state-injected, xy_eps 1e-4:", rep)
-        assert adm.all() and rep["identical_when_decided"] == 1.0
+        assert adm.all() and rep["identical_when_decided"] == 1.0 and rep["depth_within_0p5pct"] == 1.0
         state = out
+
+
+def test_north_star_bar_pooled_over_state_injected_iterations(lfd):
+    """The benchmark spec's bar, pooled over every state-injected iteration of
+    config 1 (four iterations, 900 superpixels) and of its geometry cut into
+    8-px and 5-px superpixels (two iterations each): the same chosen plane on
+    at least 99.9 % of superpixel-iterations, and depth within 0.5 % on all
+    the rest, each of which the oracle admits as a tie."""
+    import dataclasses
+    base = synth.make_config(1)
+    cases = [(base, base.params["iterations"])]
+    for pitch in (8.0, 5.0):
+        labs = []
+        for v in range(base.rig.V):
+            lab, GW, GH = synth.grid_labels(base.rig.W, base.rig.H, pitch, True, seed=2000 + v)
+            labs.append(lab)
+        cases.append((dataclasses.replace(base, labels=np.stack(labs), GW=GW, GH=GH, pitch=pitch), 2))
+    n = n_same = 0
+    for lf, iters in cases:
+        views, labels, rgb = PT.gpu_inputs(lf, "rgba8")
+        params = synth.method_params(lf, iterations=iters)
+        o = PT.make_oracle(lf, rgb, params)
+        ctx = bind(lfd, lf, views, labels, params)
+        planes, _, _ = ctx.plane_sweep()
+        state = planes.cpu().numpy()
+        items = np.arange(o.S_total, dtype=np.int32)
+        for it in range(1, iters + 1):
+            rep = {}
+            out, same, adm = _iterate_compare(lfd, ctx, o, state, it, items, rep)
+            assert adm.all() and rep["depth_within_0p5pct"] == 1.0
+            n += len(items)
+            n_same += int(same.sum())
+            state = out
+        ctx.close()
+    print(f"north_star bar pooled: {n_same} of {n} superpixel-iterations identical ({n_same / n:.5f})")
+    assert n_same >= 0.999 * n
 
 
 def test_estimate_equals_staged_and_is_deterministic(lfd, cfg1):
@@ -375,8 +413,12 @@ def test_end_to_end_config1_free_running(lfd, cfg1):
     err_o = np.median(np.abs(1 / op[m, 0] - 1 / gt[m, 0]) * gt[m, 0])
     print(f"free-running config1: identical {same.mean():.4f} depth within 0.5% {close.mean():.4f} "
           f"median rel inverse-depth error gpu {err_g:.5f} oracle {err_o:.5f}")
-    assert close.mean() >= 0.9
-    assert err_g < 0.02
+    # free-running, FP32 near-ties that go the other way change later choices,
+    # so planes drift apart in their last bits (identical 78 %); depths stay
+    # within 0.5 % on 99.9 % (bound: 99.5 %) and the accuracy matches the
+    # oracle's (0.472 % vs 0.467 %; bound: within 10 %)
+    assert close.mean() >= 0.995
+    assert abs(err_g - err_o) <= 0.1 * err_o
 
 
 def test_config2_full_size_sampled_state_injected(lfd):
@@ -393,7 +435,7 @@ def test_config2_full_size_sampled_state_injected(lfd):
     items = np.sort(rng.choice(o.S_total, size=48, replace=False)).astype(np.int32)
     sw = o.sweep(items, want_costs=True)
     c = costs.cpu().numpy().astype(np.float64)[items]
-    ok = PT.within(c, sw["cost_lo"], sw["cost_hi"])
+    ok = PT.within(c, sw["cost_lo"], sw["cost_hi"], absf=PT.tssd_abs_floor(o, items)[:, None] + PT.ABS)
     labg = lab.cpu().numpy()[items]
     adm = [labg[i] == sw["label"][i] or PT.admissible(-sw["cost_lo"][i, labg[i]], -sw["cost_hi"][i])
            for i in range(len(items)) if sw["label"][i] >= 0]
@@ -404,7 +446,7 @@ def test_config2_full_size_sampled_state_injected(lfd):
     rep = {}
     out, same, adm2 = _iterate_compare(lfd, ctx, o, state, 1, items[:24], rep)
     print("config2 iteration 1 sample:", rep)
-    assert adm2.all() and rep["identical_when_decided"] == 1.0
+    assert adm2.all() and rep["identical_when_decided"] == 1.0 and rep["depth_within_0p5pct"] == 1.0
 
 
 # ---------------------------------------------------------------------------
@@ -467,7 +509,7 @@ def test_sweep_and_iterations_across_superpixel_sizes(lfd, pitch):
         rep = {}
         out, same, adm = _iterate_compare(lfd, ctx, o, state, it, items, rep)
         print(f"pitch {pitch} iteration {it} state-injected:", rep)
-        assert adm.all() and rep["identical_when_decided"] == 1.0
+        assert adm.all() and rep["identical_when_decided"] == 1.0 and rep["depth_within_0p5pct"] == 1.0
         state = out
     if pitch >= 24.0:
         assert sizes.max() > 320          # the streamed path ran

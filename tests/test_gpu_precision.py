@@ -26,8 +26,21 @@ CASES = [
     (2, ("rgba8", "rgba_f16", "rgba_bf16", "rgba_f32")),
     (3, ("rgba_f16", "rgba_bf16", "rgba_f32")),
 ]
-# lower bounds on the sampled rates (the printed figures are the result)
-FLOOR = {"rgba8": 0.80, "rgba_f16": 0.90, "rgba_bf16": 0.75, "rgba_f32": 0.95}
+# Bounds on the sampled statistics: the observed figures (printed) less a
+# stated margin.  Labels: at most one near-tie in 32 sampled superpixels may
+# go the other way (observed 31/32 on configs 2 and 3 for every format,
+# FP32 included, and 96/96 on config 1); iteration-1 depths within 0.5 %:
+# at most one in 96 (observed all); free-running config 1 depths within
+# 0.5 %: >= 99 % (observed 99.3-99.9 %).  Median relative cost error per
+# storage format (observed: RGBA8 1.0-1.8e-4, BF16 0.6-1.4e-4, FP16
+# 1.2-1.8e-5, FP32 0.07-1.1e-5) and the share of costs inside the FP64
+# interval widened by 1e-4 for the formats whose rounding is below it
+# (observed FP32 >= 0.998, FP16 >= 0.976).
+LABEL_FLOOR = 0.95
+DEPTH_FLOOR = 0.985
+FREE_DEPTH_FLOOR = 0.99
+COST_MEDIAN_MAX = {"rgba8": 3e-4, "rgba_bf16": 2.5e-4, "rgba_f16": 4e-5, "rgba_f32": 3e-5}
+COST_INSIDE_MIN = {"rgba_f16": 0.95, "rgba_f32": 0.99}
 
 
 @pytest.fixture(scope="module")
@@ -83,5 +96,10 @@ def test_input_precision_against_fp64(lfd, cfg, fmts):
     for r in rows:
         print("  " + "  ".join(f"{k}={v:.4g}" if isinstance(v, float) else f"{k}={v}" for k, v in r.items()))
     for r in rows:
-        assert r["sweep_label_identical"] >= FLOOR[r["fmt"]] - 0.1
-        assert r["iter1_depth_0p5pct"] >= FLOOR[r["fmt"]]
+        assert r["sweep_label_identical"] >= LABEL_FLOOR
+        assert r["iter1_depth_0p5pct"] >= DEPTH_FLOOR
+        assert r["cost_rel_err_median"] <= COST_MEDIAN_MAX[r["fmt"]]
+        if r["fmt"] in COST_INSIDE_MIN:
+            assert r["cost_in_interval"] >= COST_INSIDE_MIN[r["fmt"]]
+        if "free_depth_0p5pct" in r:
+            assert r["free_depth_0p5pct"] >= FREE_DEPTH_FLOOR
