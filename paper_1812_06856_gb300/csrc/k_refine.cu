@@ -132,7 +132,10 @@ cudaError_t launch_plane_prep(const Workspace &w, const Consts &c, const float4 
 // The map holds the superpixel's mean colour times sqrt(k_col) and the depth
 // value (inverse depth, or depth in the metric domain) times sqrt(k_sig) of
 // the view's light field, so that the exponents of Eq. 7 / Eq. 9 and of the
-// Gaussian of Eq. 10 are plain squared distances in the energy kernel.
+// Gaussian of Eq. 10 are plain squared distances in the energy kernel.  (An
+// 8-B texel {depth value, superpixel} with the colours in a table halves the
+// gathered bytes but adds a dependent gather per sample: measured 17-19 %
+// slower on the 8 x 1024x768 and 16 x 1080p frames.)
 
 __global__ void __launch_bounds__(128) k_rasterize(Workspace w, Consts c, float *const *depth)
 {
@@ -215,7 +218,9 @@ struct WarpSP {
 };
 
 struct alignas(16) SpShared {
-    float2 px[32 * SLOTS_MAX];           // pixel offsets from ref of the first 32*SLOTS_MAX pixels
+    // offsets from ref of the first 32*SLOTS_MAX pixels, two slots per entry:
+    // px4[32 jp + lane] = (du, du', dv, dv') of pixels lane + 64 jp and lane + 64 jp + 32
+    float4 px4[32 * (SLOTS_MAX / 2)];
     WarpSP S;
     SpView view[LFD_MAXN];
     SpNb nb[8];
@@ -318,13 +323,57 @@ __device__ __forceinline__ HypF cand_load(const CandShared &cs, int src)
     return h;
 }
 
-// One pixel-view sample of Eq. 9-11, branch-free so that the samples of an
-// unrolled loop keep their gathers in flight together; `act` false (a lane
-// past the superpixel's last pixel) contributes nothing.  gp: the
-// hypothesis' inverse depth at the pixel.  Map colours and depth values carry
-// sqrt(k_col) and sqrt(k_sig); the homography rows carry 1/sqrt(k_sig)
-// (inverse-depth domain: 1/z_i = gp / Nw comes out scaled) or sqrt(k_sig)
-// (metric: z_i = Nw / gp), which leaves the pixel position fx, fy unchanged.
+// The part of one pixel-view sample of Eq. 9-11 after the projection:
+// nearest pixel, window, gathers, sums.  Branch-free so that the samples of
+// an unrolled loop keep their gathers in flight together; `act` false (a
+// lane past the superpixel's last pixel) contributes nothing.  Nw: camera-i
+// depth times g.p; r = 1/Nw; tx, ty: the offsets from the integer anchor
+// plus 1.5 * 2^23 (see below); gp: the hypothesis' inverse depth at the
+// pixel; val0 = gp r (inverse-depth domain).  Map colours and depth values
+// carry sqrt(k_col) and sqrt(k_sig); the homography rows carry
+// 1/sqrt(k_sig) (inverse-depth domain: 1/z_i = gp / Nw comes out scaled) or
+// sqrt(k_sig) (metric: z_i = Nw / gp), which leaves the pixel position
+// unchanged.
+template <int DOMAIN>
+__device__ __forceinline__ void sample_tail(const ViewK &K, bool act, float Nw, float tx, float ty, float gp,
+                                            float val0, float cr, float cg, float cb, Acc &a)
+{
+    // Nearest pixel: adding 1.5 * 2^23 rounds an offset |f| < 2^22 to an
+    // integer held in the low mantissa bits (ties to even: the oracle flags
+    // an exact .5 as a rounding boundary where either pixel is admissible).
+    // The point lies in view i iff that pixel does (-1/2 <= x < W - 1/2);
+    // out-of-range or non-finite offsets give out-of-range integers.
+    const int ix = __float_as_int(tx) + K.xa_m;
+    const int iy = __float_as_int(ty) + K.ya_m;
+    const bool ok = act && (gp > 0.f) && (Nw > 0.f) && ((unsigned)ix < (unsigned)K.Wi) &&
+                    ((unsigned)iy < (unsigned)K.Hi);
+    const int idx = ok ? iy * K.Wi + ix : 0;                     // in-bounds address either way
+    const float4 c = __ldg(K.map + idx);                         // {colour of the superpixel hit, depth value}
+    const float tw = c.w;
+    const float dr = c.x - cr, dg = c.y - cg, db = c.z - cb;
+    const float om = ex2_approx(-fmaf(dr, dr, fmaf(dg, dg, db * db)));   // Eq. 9 summand
+    a.cnt += ok ? 1u : 0u;
+    a.sw += ok ? om : 0.f;
+    const bool has = ok && tw > 0.f;
+    float val;
+    bool inX;
+    if (DOMAIN == 0) {
+        val = val0;                                              // 1 / z_i(P), scaled
+        inX = has && val >= tw * K.xy;
+    } else {
+        val = Nw * rcp_approx(gp);                               // z_i(P), scaled
+        inX = has && val <= tw * K.xy;
+    }
+    const float dd = val - tw;
+    const float G = ex2_approx(-dd * dd);                        // Eq. 10 summand
+    a.nx += inX ? 1u : 0u;
+    a.sg += inX ? G : 0.f;
+    a.ny += (has && !inX) ? 1u : 0u;
+}
+
+constexpr float ROUND_MAGIC = 12582912.0f;                      // 1.5 * 2^23
+
+// one sample: projection of pixel offset (du, dv) into view i, then the tail
 template <int DOMAIN>
 __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du, float dv, float gp, float cr,
                                               float cg, float cb, Acc &a)
@@ -333,37 +382,7 @@ __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du
     const float ex = fmaf(K.b0, du, fmaf(K.b1, dv, K.cx));
     const float ey = fmaf(K.c0, du, fmaf(K.c1, dv, K.cy));
     const float r = rcp_approx(Nw);
-    const float fx = ex * r, fy = ey * r;                        // offsets from the integer anchor
-    // Nearest pixel: adding 1.5 * 2^23 rounds an offset |f| < 2^22 to an
-    // integer held in the low mantissa bits (ties to even: the oracle flags
-    // an exact .5 as a rounding boundary where either pixel is admissible).
-    // The point lies in view i iff that pixel does (-1/2 <= x < W - 1/2);
-    // out-of-range or non-finite offsets give out-of-range integers.
-    const int ix = __float_as_int(fx + 12582912.0f) + K.xa_m;
-    const int iy = __float_as_int(fy + 12582912.0f) + K.ya_m;
-    const bool ok = act && (gp > 0.f) && (Nw > 0.f) && ((unsigned)ix < (unsigned)K.Wi) &&
-                    ((unsigned)iy < (unsigned)K.Hi);
-    const int idx = ok ? iy * K.Wi + ix : 0;                     // in-bounds address either way
-    const float4 t = __ldg(K.map + idx);
-    const float dr = t.x - cr, dg = t.y - cg, db = t.z - cb;
-    const float om = ex2_approx(-fmaf(dr, dr, fmaf(dg, dg, db * db)));   // Eq. 9 summand
-    a.cnt += ok ? 1u : 0u;
-    a.sw += ok ? om : 0.f;
-    const bool has = ok && t.w > 0.f;
-    float val;
-    bool inX;
-    if (DOMAIN == 0) {
-        val = gp * r;                                            // 1 / z_i(P), scaled
-        inX = has && val >= t.w * K.xy;
-    } else {
-        val = Nw * rcp_approx(gp);                               // z_i(P), scaled
-        inX = has && val <= t.w * K.xy;
-    }
-    const float dd = val - t.w;
-    const float G = ex2_approx(-dd * dd);                        // Eq. 10 summand
-    a.nx += inX ? 1u : 0u;
-    a.sg += inX ? G : 0.f;
-    a.ny += (has && !inX) ? 1u : 0u;
+    sample_tail<DOMAIN>(K, act, Nw, fmaf(ex, r, ROUND_MAGIC), fmaf(ey, r, ROUND_MAGIC), gp, gp * r, cr, cg, cb, a);
 }
 
 // The view terms V_i + O_i (Eq. 9-11) of every candidate of `mask` (a batch
@@ -405,11 +424,17 @@ __device__ __noinline__ void view_terms(const Workspace &w, unsigned mask, float
             K.map = sv.map;
             K.xy = DOMAIN == 0 ? sh.xy_lo : sh.xy_hi;
             Acc a = {0u, 0u, 0u, 0.f, 0.f};
+            // slots j and j + 1 come from one shared-memory load; every slot
+            // but the last is full unless MASK_ALL
 #pragma unroll
-            for (int j = 0; j < SL; j++) {
-                const float2 d = sh.px[32 * j + lane];
-                energy_sample<DOMAIN>(K, (!MASK_ALL && j + 1 < SL) || lane + 32 * j < S.n, d.x, d.y,
-                                      fmaf(h.g0, d.x, fmaf(h.g1, d.y, h.gr)), S.cr, S.cg, S.cb, a);
+            for (int jp = 0; jp < (SL + 1) / 2; jp++) {
+                const int j0 = 2 * jp, j1 = 2 * jp + 1;
+                const float4 d = sh.px4[32 * jp + lane];
+                energy_sample<DOMAIN>(K, (!MASK_ALL && j0 + 1 < SL) || lane + 32 * j0 < S.n, d.x, d.z,
+                                      fmaf(h.g0, d.x, fmaf(h.g1, d.z, h.gr)), S.cr, S.cg, S.cb, a);
+                if (j1 < SL)
+                    energy_sample<DOMAIN>(K, (!MASK_ALL && j1 + 1 < SL) || lane + 32 * j1 < S.n, d.y, d.w,
+                                          fmaf(h.g0, d.y, fmaf(h.g1, d.w, h.gr)), S.cr, S.cg, S.cb, a);
             }
             if (SL == SLOTS_MAX) {
 #pragma unroll 2
@@ -583,14 +608,20 @@ __device__ bool setup_sp(const Workspace &w, const float4 *planes_in, int gs, in
 
     // pixel offsets of the first 32*SLOTS_MAX pixels (zero past the last pixel)
 #pragma unroll
-    for (int j = 0; j < SLOTS_MAX; j++) {
-        const int i = lane + 32 * j;
-        float2 d = make_float2(0.f, 0.f);
-        if (i < S.n) {
-            const unsigned pk = __ldg(w.sp_pix + S.off + i);
-            d = make_float2((float)((int)(pk & 0xffff) - S.ref.x), (float)((int)(pk >> 16) - S.ref.y));
+    for (int jp = 0; jp < SLOTS_MAX / 2; jp++) {
+        float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int i0 = lane + 64 * jp, i1 = i0 + 32;
+        if (i0 < S.n) {
+            const unsigned pk = __ldg(w.sp_pix + S.off + i0);
+            d.x = (float)((int)(pk & 0xffff) - S.ref.x);
+            d.z = (float)((int)(pk >> 16) - S.ref.y);
         }
-        sh.px[i] = d;
+        if (i1 < S.n) {
+            const unsigned pk = __ldg(w.sp_pix + S.off + i1);
+            d.y = (float)((int)(pk & 0xffff) - S.ref.x);
+            d.w = (float)((int)(pk >> 16) - S.ref.y);
+        }
+        sh.px4[32 * jp + lane] = d;
     }
     if (lane == 0) sh.S = S;
     __syncwarp();
@@ -975,7 +1006,7 @@ __global__ void __launch_bounds__(128) k_score(const __grid_constant__ Workspace
             const unsigned pk = __ldg(w.sp_pix + S.off + i);
             const int x = pk & 0xffff, y = pk >> 16;
             const float du = (float)(x - S.ref.x), dv = (float)(y - S.ref.y);
-            const float3 rc = texel_colour<FMT>(vd.quad, (long long)y * vd.W + x, (long long)vd.W * vd.H);
+            const float3 rc = texel_colour<FMT>(vd.quad, x, y, vd.W, vd.H);
             const float gp = (float)(g0 * x + g1 * y + g2);
             float t = vd.T;
             if (gp > 0.f) {

@@ -290,9 +290,10 @@ cudaError_t launch_sp_minw(const Workspace &w, const Consts &c, float4 *col, cud
 // 5. sampling textures: per pixel the 2x2 bilinear footprint in one record
 // ---------------------------------------------------------------------------
 //   RGBA8: bilinear coefficients as exact halves               24 B / pixel
-//          (16-B records for all pixels, then 8-B records)
+//          (16-B records for all entries, then 8-B records)
 //   F16/BF16: 2 x uint4 {t00, t10}, {t01, t11} (8 B texels)  32 B / pixel
 //   F32: 3 x float4 RGB of t00, t10, t01, t11                48 B / pixel
+//   (W + 1) x (H + 1) entries per view, see k_quads
 
 __device__ __forceinline__ unsigned pack_h2(float lo, float hi)
 {
@@ -300,14 +301,22 @@ __device__ __forceinline__ unsigned pack_h2(float lo, float hi)
     return *reinterpret_cast<unsigned *>(&h);
 }
 
+// The texture has a border of one quad on the left and top: entry
+// (y + 1) (W + 1) + (x + 1) holds the quad of pixel (x, y) for x in [-1, W-1],
+// y in [-1, H-1], every texel index clamped to the image.  A bilinear sample
+// anywhere in the texture area -1/2 <= x < W - 1/2 then reads the quad at
+// floor(x) with no clamping of the coordinates: where a texel is clamped its
+// difference to the neighbour is 0, which gives clamp-to-edge exactly.
 __global__ void __launch_bounds__(256) k_quads(Workspace w, int fmt)
 {
     const int v = blockIdx.y;
     const ViewDev &vd = w.views[v];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= vd.W * vd.H) return;
-    const int x = p % vd.W, y = p / vd.W;
-    const int x1 = min(x + 1, vd.W - 1), y1 = min(y + 1, vd.H - 1);
+    const int Wp = vd.W + 1;
+    if (p >= Wp * (vd.H + 1)) return;
+    const int qx = p % Wp - 1, qy = p / Wp - 1;
+    const int x = max(qx, 0), y = max(qy, 0);
+    const int x1 = min(qx + 1, vd.W - 1), y1 = min(qy + 1, vd.H - 1);
     const char *base = (const char *)vd.img;
     const long long pitch = vd.pitch;
     const char *r0 = base + (long long)y * pitch;
@@ -324,7 +333,7 @@ __global__ void __launch_bounds__(256) k_quads(Workspace w, int fmt)
             by[ch] = (float)(c01[ch] - c00[ch]);
             bxy[ch] = (float)(c11[ch] - c10[ch] - c01[ch] + c00[ch]);
         }
-        const long long npx = (long long)vd.W * vd.H;
+        const long long npx = (long long)Wp * (vd.H + 1);
         ((uint4 *)vd.quad)[p] = make_uint4(pack_h2(av[0], av[1]), pack_h2(av[2], bx[0]), pack_h2(bx[1], bx[2]),
                                            pack_h2(by[0], by[1]));
         ((uint2 *)((uint4 *)vd.quad + npx))[p] = make_uint2(pack_h2(by[2], bxy[0]), pack_h2(bxy[1], bxy[2]));
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(256) k_quads(Workspace w, int fmt)
 
 cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStream_t st)
 {
-    dim3 grid((max_px + 255) / 256, V);
+    dim3 grid((max_px + 255) / 256, V);       // max_px: largest (W + 1) (H + 1) of the views
     k_quads<<<grid, 256, 0, st>>>(w, fmt);
     return cudaGetLastError();
 }
@@ -367,24 +376,33 @@ cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStr
 //    and read 6x more DRAM).  Deterministic.
 // ---------------------------------------------------------------------------
 
-constexpr int ORDER_KEYS = 17;
+//    Inside a class the superpixels go by row band (ORDER_BANDS bands of
+//    each view's grid rows) and then in index order: the superpixels in
+//    flight at any time cover the same rows of every view, so the rows of
+//    the sampling textures and rasterised maps they gather from (their own
+//    band, shifted by the disparity, in each neighbour view) stay in L2
+//    together instead of spanning whole views.
 
 __device__ __forceinline__ int order_key(const Workspace &w, int gs, int mode)
 {
     const int n = __ldg(w.sp_cnt + gs);
     const int cls = mode == 0 ? (n + 31) >> 5 : 31 - __clz(max(n, 1));
-    return ORDER_KEYS - 1 - min(cls, ORDER_KEYS - 1);    // 0 = largest class
+    const ViewDev &vd = w.views[__ldg(w.sp_view + gs)];
+    const int gy = (gs - vd.sp_base) / vd.GW;
+    const int band = min(ORDER_BANDS - 1, (int)(((long long)gy * ORDER_BANDS) / vd.GH));
+    return (ORDER_CLASSES - 1 - min(cls, ORDER_CLASSES - 1)) * ORDER_BANDS + band;   // 0 = largest class, top band
 }
 
 __global__ void k_order_hist(Workspace w, int *hist, int mode)
 {
     __shared__ int h[ORDER_KEYS];
-    if (threadIdx.x < ORDER_KEYS) h[threadIdx.x] = 0;
+    for (int k = threadIdx.x; k < ORDER_KEYS; k += blockDim.x) h[k] = 0;
     __syncthreads();
     const int gs = blockIdx.x * blockDim.x + threadIdx.x;
     if (gs < w.S_total) atomicAdd(&h[order_key(w, gs, mode)], 1);
     __syncthreads();
-    if (threadIdx.x < ORDER_KEYS && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+    for (int k = threadIdx.x; k < ORDER_KEYS; k += blockDim.x)
+        if (h[k]) atomicAdd(&hist[k], h[k]);
 }
 
 // one CTA of 1024 threads walks the superpixels in tiles of 1024; a

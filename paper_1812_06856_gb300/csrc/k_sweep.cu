@@ -134,7 +134,7 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
                 const unsigned pk = __ldg(w.sp_pix + off + pc + i);
                 const int x = pk & 0xffff, y = pk >> 16;
                 sh.d[i] = make_float2((float)(x - ref.x), (float)(y - ref.y));
-                const float3 rc = texel_colour<FMT>(own_tex, (long long)y * vd.W + x, (long long)vd.W * vd.H);
+                const float3 rc = texel_colour<FMT>(own_tex, x, y, vd.W, vd.H);
                 float front = 1.f;
                 if (WORLD) front = (sh.gh[0] * x + sh.gh[1] * y + sh.gh[2]) > 0.0 ? 1.f : 0.f;
                 sh.ref[i] = make_float4(rc.x, rc.y, rc.z, front);

@@ -422,7 +422,7 @@ cudaError_t traced(lfd_ctx *ctx, int stage, cudaStream_t st, F launch, int kerne
 }
 
 // -- layout + workspace allocation -------------------------------------------
-constexpr int ORDER_KEYS_HOST = 17;   // size classes of the work order
+constexpr int ORDER_KEYS_HOST = ORDER_KEYS;   // keys of the work orders' counting sort
 
 // Sizes of the bound views in call order (global numbering).
 lfd_status make_layout(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, Layout &L)
@@ -466,7 +466,7 @@ size_t workspace_need(const Layout &L, int fmt)
     add(sizeof(DevCounters));
     add(4 * S); add(4 * S); add(4 * ORDER_KEYS_HOST); add(16); add(sizeof(float *) * V);
     add(16 * S); add(16 * S); add(4 * S); add(8 * S); add(8 * S);
-    for (int v = 0; v < V; v++) add((size_t)qb * L.W[v] * L.H[v]);
+    for (int v = 0; v < V; v++) add((size_t)qb * (L.W[v] + 1) * (L.H[v] + 1));
     for (int v = 0; v < V; v++) add((size_t)16 * L.W[v] * L.H[v]);
     return need + 256;
 }
@@ -534,7 +534,7 @@ lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
     ctx->d_energy = (float *)a.take(8 * S);
     ctx->quads.assign(V, nullptr);
     ctx->maps.assign(V, nullptr);
-    for (int v = 0; v < V; v++) ctx->quads[v] = a.take((size_t)qb * L.W[v] * L.H[v]);
+    for (int v = 0; v < V; v++) ctx->quads[v] = a.take((size_t)qb * (L.W[v] + 1) * (L.H[v] + 1));
     for (int v = 0; v < V; v++) ctx->maps[v] = (float4 *)a.take((size_t)16 * L.W[v] * L.H[v]);
     ctx->L = L;
     Workspace &w = ctx->w;
@@ -717,7 +717,9 @@ lfd_status enqueue_input(lfd_ctx *ctx, cudaStream_t st, bool record_event)
                                  ctx->d_sp_ref, ctx->d_sp_col, st);
     }));
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_sp_minw(ctx->w, ctx->c, ctx->d_sp_col, st); }));
-    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_quads(ctx->w, V, L.max_px, ctx->fmt, st); }));
+    int max_quads = 0;
+    for (int v = 0; v < V; v++) max_quads = std::max(max_quads, (L.W[v] + 1) * (L.H[v] + 1));
+    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_quads(ctx->w, V, max_quads, ctx->fmt, st); }));
     // work orders: propagation by descending slot class, the sweep by descending
     // power-of-two size class, index order inside a class
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st,

@@ -144,6 +144,44 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// Blackwell packed single precision (sm_100 and later): two IEEE binary32
+// operations, each rounded to nearest like its scalar form, in one
+// instruction (the sweep interpolates red and green as a pair).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%6, %7};\n\t"
+        "fma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mul.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
+
 // exact byte -> float through the 2^23 mantissa trick (byte c of w)
 template <int C>
 __device__ __forceinline__ float u8_to_f(unsigned w)
@@ -217,7 +255,11 @@ cudaError_t launch_sp_collect(const Workspace &w, const Consts &c, const int4 *b
 cudaError_t launch_sp_minw(const Workspace &w, const Consts &c, float4 *col, cudaStream_t st);
 cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStream_t st);
 // mode 0: pixel-slot classes ceil(n/32) (propagation); mode 1: power-of-two classes floor(log2 n) (sweep)
-cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, cudaStream_t st);  // hist: 17 ints
+// keys of the work orders' counting sort: 17 size classes x 16 row bands
+constexpr int ORDER_CLASSES = 17;
+constexpr int ORDER_BANDS = 16;
+constexpr int ORDER_KEYS = ORDER_CLASSES * ORDER_BANDS;
+cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, cudaStream_t st);  // hist: ORDER_KEYS ints
 cudaError_t launch_sweep(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
                          float *cost, cudaStream_t st);
 cudaError_t launch_plane_prep(const Workspace &w, const Consts &c, const float4 *planes, double4_32a *g, float4 *rc,

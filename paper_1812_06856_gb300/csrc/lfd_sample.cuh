@@ -45,53 +45,68 @@ __device__ __forceinline__ float2 bf2f(unsigned u)
     return __bfloat1622float2(h);
 }
 
+// The 2x2 texels of a float quad: rg[k] = (red, green) of texel k (k = 0
+// (x,y), 1 (x+1,y), 2 (x,y+1), 3 (x+1,y+1)) as a pair for the packed
+// arithmetic, b[k] its blue.
 template <>
 struct Quad<LFD_RGBA_F16> {
-    float r[4], g[4], b[4];
+    float2 rg[4];
+    float b[4];
     __device__ __forceinline__ void load(const void *tex, long long idx)
     {
         const uint4 *q = (const uint4 *)tex + 2 * idx;
         const uint4 a = __ldg(q), c = __ldg(q + 1);
-        float2 t;
-        t = h2f(a.x); r[0] = t.x; g[0] = t.y; b[0] = h2f(a.y).x;
-        t = h2f(a.z); r[1] = t.x; g[1] = t.y; b[1] = h2f(a.w).x;
-        t = h2f(c.x); r[2] = t.x; g[2] = t.y; b[2] = h2f(c.y).x;
-        t = h2f(c.z); r[3] = t.x; g[3] = t.y; b[3] = h2f(c.w).x;
+        rg[0] = h2f(a.x); b[0] = h2f(a.y).x;
+        rg[1] = h2f(a.z); b[1] = h2f(a.w).x;
+        rg[2] = h2f(c.x); b[2] = h2f(c.y).x;
+        rg[3] = h2f(c.z); b[3] = h2f(c.w).x;
     }
 };
 
 template <>
 struct Quad<LFD_RGBA_BF16> {
-    float r[4], g[4], b[4];
+    float2 rg[4];
+    float b[4];
     __device__ __forceinline__ void load(const void *tex, long long idx)
     {
         const uint4 *q = (const uint4 *)tex + 2 * idx;
         const uint4 a = __ldg(q), c = __ldg(q + 1);
-        float2 t;
-        t = bf2f(a.x); r[0] = t.x; g[0] = t.y; b[0] = bf2f(a.y).x;
-        t = bf2f(a.z); r[1] = t.x; g[1] = t.y; b[1] = bf2f(a.w).x;
-        t = bf2f(c.x); r[2] = t.x; g[2] = t.y; b[2] = bf2f(c.y).x;
-        t = bf2f(c.z); r[3] = t.x; g[3] = t.y; b[3] = bf2f(c.w).x;
+        rg[0] = bf2f(a.x); b[0] = bf2f(a.y).x;
+        rg[1] = bf2f(a.z); b[1] = bf2f(a.w).x;
+        rg[2] = bf2f(c.x); b[2] = bf2f(c.y).x;
+        rg[3] = bf2f(c.z); b[3] = bf2f(c.w).x;
     }
 };
 
 template <>
 struct Quad<LFD_RGBA_F32> {
-    float r[4], g[4], b[4];
+    float2 rg[4];
+    float b[4];
     __device__ __forceinline__ void load(const void *tex, long long idx)
     {
         const float4 *q = (const float4 *)tex + 3 * idx;
         const float4 a = __ldg(q), c = __ldg(q + 1), d = __ldg(q + 2);
-        r[0] = a.x; g[0] = a.y; b[0] = a.z; r[1] = a.w;
-        g[1] = c.x; b[1] = c.y; r[2] = c.z; g[2] = c.w;
-        b[2] = d.x; r[3] = d.y; g[3] = d.z; b[3] = d.w;
+        rg[0] = make_float2(a.x, a.y); b[0] = a.z;
+        rg[1] = make_float2(a.w, c.x); b[1] = c.y;
+        rg[2] = make_float2(c.z, c.w); b[2] = d.x;
+        rg[3] = make_float2(d.y, d.z); b[3] = d.w;
     }
 };
 
-// colour of pixel (x,y) itself (texel t00 of its quad); npx = pixels of the view
-template <int FMT>
-__device__ __forceinline__ float3 texel_colour(const void *tex, long long idx, long long npx)
+// entry of pixel (x, y) in a view's sampling texture (a border of one quad
+// on the left and top, (W + 1) x (H + 1) entries; see k_quads)
+__device__ __forceinline__ long long quad_index(int x, int y, int W)
 {
+    return (long long)(y + 1) * (W + 1) + (x + 1);
+}
+
+__device__ __forceinline__ long long quad_entries(int W, int H) { return (long long)(W + 1) * (H + 1); }
+
+// colour of pixel (x,y) itself (texel t00 of its quad)
+template <int FMT>
+__device__ __forceinline__ float3 texel_colour(const void *tex, int x, int y, int W, int H)
+{
+    const long long idx = quad_index(x, y, W), npx = quad_entries(W, H);
     if constexpr (FMT == LFD_RGBA8) {
         const uint4 q = __ldg((const uint4 *)tex + idx);
         const float2 t0 = h2f(q.x), t1 = h2f(q.y);
@@ -99,7 +114,7 @@ __device__ __forceinline__ float3 texel_colour(const void *tex, long long idx, l
     } else {
         Quad<FMT> q;
         q.load(tex, idx);
-        return make_float3(q.r[0], q.g[0], q.b[0]);
+        return make_float3(q.rg[0].x, q.rg[0].y, q.b[0]);
     }
 }
 
@@ -107,40 +122,41 @@ __device__ __forceinline__ float3 texel_colour(const void *tex, long long idx, l
 // bilinearly at the homogeneous point (X, Y, Wz); T when the point is behind
 // camera i (Wz <= 0) or off the image's texture area -1/2 <= x < Wi - 1/2,
 // -1/2 <= y < Hi - 1/2 (its nearest pixel is not a pixel of view i).  Inside,
-// the coordinates are clamped to the outermost pixel centres (clamp to edge).
+// the texture's border quads give clamp-to-edge (see k_quads).
 template <int FMT>
 __device__ __forceinline__ float tssd_sample(const void *tex, int Wi, int Hi, float X, float Y, float Wz, float3 ref,
                                              float T)
 {
     const float rw = rcp_approx(Wz);
-    const float xr = X * rw, yr = Y * rw;
-    const bool ok = (Wz > 0.f) && (xr >= -0.5f) && (xr < (float)Wi - 0.5f) && (yr >= -0.5f) &&
-                    (yr < (float)Hi - 0.5f);
+    const float x = X * rw, y = Y * rw;
+    const bool ok = (Wz > 0.f) && (x >= -0.5f) && (x < (float)Wi - 0.5f) && (y >= -0.5f) && (y < (float)Hi - 0.5f);
     if (!ok) return T;
-    const float x = fminf(fmaxf(xr, 0.f), (float)(Wi - 1)), y = fminf(fmaxf(yr, 0.f), (float)(Hi - 1));
-    const float xf = floorf(x), yf = floorf(y);
+    const float xf = floorf(x), yf = floorf(y);          // -1 .. W-1, -1 .. H-1
     const float fx = x - xf, fy = y - yf;
-    const long long idx = (long long)(int)yf * Wi + (int)xf;
-    float dr, dg, db;
+    const long long idx = quad_index((int)xf, (int)yf, Wi);
     if constexpr (FMT == LFD_RGBA8) {
         Coef8 q;
-        q.load(tex, idx, (long long)Wi * Hi);
+        q.load(tex, idx, quad_entries(Wi, Hi));
         const float fxy = fx * fy;
-        dr = ref.x - fmaf(fxy, q.bxy[0], fmaf(fy, q.by[0], fmaf(fx, q.bx[0], q.a[0])));
-        dg = ref.y - fmaf(fxy, q.bxy[1], fmaf(fy, q.by[1], fmaf(fx, q.bx[1], q.a[1])));
-        db = ref.z - fmaf(fxy, q.bxy[2], fmaf(fy, q.by[2], fmaf(fx, q.bx[2], q.a[2])));
+        const float dr = ref.x - fmaf(fxy, q.bxy[0], fmaf(fy, q.by[0], fmaf(fx, q.bx[0], q.a[0])));
+        const float dg = ref.y - fmaf(fxy, q.bxy[1], fmaf(fy, q.by[1], fmaf(fx, q.bx[1], q.a[1])));
+        const float db = ref.z - fmaf(fxy, q.bxy[2], fmaf(fy, q.by[2], fmaf(fx, q.bx[2], q.a[2])));
+        return fminf(fmaf(dr, dr, fmaf(dg, dg, db * db)), T);
     } else {
+        // red and green as packed pairs, blue alone: the same lerps as scalar
+        // code, half the issue slots for two of the channels
         Quad<FMT> q;
         q.load(tex, idx);
-        const float r0 = fmaf(fx, q.r[1] - q.r[0], q.r[0]), r1 = fmaf(fx, q.r[3] - q.r[2], q.r[2]);
-        const float g0 = fmaf(fx, q.g[1] - q.g[0], q.g[0]), g1 = fmaf(fx, q.g[3] - q.g[2], q.g[2]);
+        const float2 FX = dup2(fx);
+        const float2 top = ffma2(FX, fsub2(q.rg[1], q.rg[0]), q.rg[0]);
+        const float2 bot = ffma2(FX, fsub2(q.rg[3], q.rg[2]), q.rg[2]);
+        const float2 rg = ffma2(dup2(fy), fsub2(bot, top), top);
         const float b0 = fmaf(fx, q.b[1] - q.b[0], q.b[0]), b1 = fmaf(fx, q.b[3] - q.b[2], q.b[2]);
-        dr = ref.x - fmaf(fy, r1 - r0, r0);
-        dg = ref.y - fmaf(fy, g1 - g0, g0);
-        db = ref.z - fmaf(fy, b1 - b0, b0);
+        const float2 d = fsub2(make_float2(ref.x, ref.y), rg);
+        const float2 d2 = fmul2(d, d);
+        const float db = ref.z - fmaf(fy, b1 - b0, b0);
+        return fminf(fmaf(db, db, d2.x + d2.y), T);
     }
-    const float ssd = fmaf(dr, dr, fmaf(dg, dg, db * db));
-    return fminf(ssd, T);
 }
 
 }  // namespace lfd
