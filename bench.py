@@ -548,8 +548,13 @@ def mix_workload_name(n: int, scale: float) -> str:
             f"pitch 8-32 px, 128-256 labels, 6 iterations")
 
 
+TUNE = {"autotune": 1}     # the first (warm-up) call of the batched workload tunes its launch shape
+
+
 def run_ours_batch(args):
-    """Config 4: one step = one lfd_estimate_batch call over all light fields."""
+    """Config 4: one step = one lfd_estimate_batch call over all light fields,
+    launch shape chosen by the library's autotuner on the first (warm-up)
+    call."""
     ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
@@ -564,10 +569,10 @@ def run_ours_batch(args):
     ctx = lfd.Context(local)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    out = None
-    for _ in range(max(args.warmup, 1)):
+    out = ctx.estimate_batch(items)                   # allocates the outputs the timed calls reuse
+    for _ in range(max(args.warmup, 1)):             # the first of these tunes (same signature after)
         flush.fill_(1)
-        out = ctx.estimate_batch(items, out=out)
+        out = ctx.estimate_batch(items, out=out, options=TUNE)
     ctx.synchronize()
     hyp_step, samples_step = ctx.counters()
     ctx.profile_read()
@@ -588,7 +593,7 @@ def run_ours_batch(args):
     for k in range(args.steps):
         flush.fill_(k & 0xff)
         ev[k][0].record(stream)
-        ctx.estimate_batch(items, out=out)
+        ctx.estimate_batch(items, out=out, options=TUNE)
         ev[k][1].record(stream)
     barrier()
     clock_info = clocks.stop()
@@ -629,7 +634,7 @@ def run_ours_batch(args):
             for m, a, b in zip(mix, vh, lh):
                 m.views.copy_(a, non_blocking=True)
                 m.labels.copy_(b, non_blocking=True)
-            ctx.estimate_batch(items, out=out)
+            ctx.estimate_batch(items, out=out, options=TUNE)
             ph.copy_(out[0], non_blocking=True)
             for a, b in zip(dh, out[1]):
                 a.copy_(b, non_blocking=True)

@@ -291,12 +291,14 @@ lfd_status lfd_fuse(lfd_ctx *ctx, const float *const *depth_in, float *const *de
 
 /* Launch options of lfd_estimate_batch (lfd_batch_options_default fills
  * autotune 0, graph 0, sweep_threads 256, sweep_persistent 1, prop_blocks 8,
- * prop_persistent 1). */
+ * prop_persistent 1, prop_batch 32, order_bands 16). */
 typedef struct {
-    int32_t autotune;          /* 1: the first call with a new argument signature times the
-                                  sweep (128/256 threads x grid/persistent) and propagation
-                                  (7/8 CTAs per SM x grid/persistent) launch shapes on its own
-                                  input and keeps the fastest; the shape fields are then ignored */
+    int32_t autotune;          /* 1: the first call with a new argument signature times, on its
+                                  own input, the sweep (128/256 threads x grid/persistent x
+                                  1/16 row bands in the work order) and the propagation (7/8
+                                  CTAs per SM x grid/persistent x 16/32 candidates per batch x
+                                  1/16 row bands) and keeps the fastest of each; the shape
+                                  fields are then ignored */
     int32_t graph;             /* 1: the frame's device work is captured as a CUDA graph on the
                                   first call; a later call whose signature (every pointer, size,
                                   camera, parameter and option) is identical replays it, reading
@@ -307,7 +309,10 @@ typedef struct {
                                   by size (pixel-slot class ceil(n/32)), largest first */
     int32_t prop_blocks;       /* 7 or 8 (0 = 8) resident propagation CTAs per SM */
     int32_t prop_persistent;   /* 1: persistent propagation warps over the same ordered queue */
-    int32_t reserved[2];       /* must be 0 */
+    int32_t prop_batch;        /* 16 or 32 (0 = 32): candidate planes a warp scores per pass over the
+                                  neighbour views (their footprints share L1 across the pass) */
+    int32_t order_bands;       /* 1 or 16 (0 = 16): row bands of the work orders inside a size class
+                                  (16: the superpixels in flight cover the same rows of every view) */
 } lfd_batch_options;
 
 void lfd_batch_options_default(lfd_batch_options *o);
@@ -352,8 +357,8 @@ lfd_status lfd_estimate_batch_warm(lfd_ctx *ctx, int32_t n, const lfd_lightfield
  * cameras, grid sizes and pixel format. */
 lfd_status lfd_workspace_required(int32_t n, const lfd_lightfield *lfs, uint64_t *bytes);
 
-/* The launch shape in use: out[0..3] = sweep_threads, sweep_persistent,
- * prop_blocks, prop_persistent. */
+/* The launch shape in use: out[0..5] = sweep_threads, sweep_persistent,
+ * prop_blocks, prop_persistent, prop_batch, order_bands. */
 lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out);
 
 /* ---- serving ---------------------------------------------------------- */

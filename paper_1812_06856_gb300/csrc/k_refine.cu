@@ -334,7 +334,7 @@ __device__ __forceinline__ HypF cand_load(const CandShared &cs, int src)
 // 1/sqrt(k_sig) (inverse-depth domain: 1/z_i = gp / Nw comes out scaled) or
 // sqrt(k_sig) (metric: z_i = Nw / gp), which leaves the pixel position
 // unchanged.
-template <int DOMAIN>
+template <int DOMAIN, bool CHECKW = true>
 __device__ __forceinline__ void sample_tail(const ViewK &K, bool act, float Nw, float tx, float ty, float gp,
                                             float val0, float cr, float cg, float cb, Acc &a)
 {
@@ -345,7 +345,7 @@ __device__ __forceinline__ void sample_tail(const ViewK &K, bool act, float Nw, 
     // out-of-range or non-finite offsets give out-of-range integers.
     const int ix = __float_as_int(tx) + K.xa_m;
     const int iy = __float_as_int(ty) + K.ya_m;
-    const bool ok = act && (gp > 0.f) && (Nw > 0.f) && ((unsigned)ix < (unsigned)K.Wi) &&
+    const bool ok = act && (gp > 0.f) && (!CHECKW || Nw > 0.f) && ((unsigned)ix < (unsigned)K.Wi) &&
                     ((unsigned)iy < (unsigned)K.Hi);
     const int idx = ok ? iy * K.Wi + ix : 0;                     // in-bounds address either way
     const float4 c = __ldg(K.map + idx);                         // {colour of the superpixel hit, depth value}
@@ -373,16 +373,20 @@ __device__ __forceinline__ void sample_tail(const ViewK &K, bool act, float Nw, 
 
 constexpr float ROUND_MAGIC = 12582912.0f;                      // 1.5 * 2^23
 
-// one sample: projection of pixel offset (du, dv) into view i, then the tail
-template <int DOMAIN>
+// one sample: projection of pixel offset (du, dv) into view i, then the
+// tail.  AFF (affine pair: a20 = a21 = 0, so Nw = hw for every pixel): Nw and
+// r = 1/hw come from the caller, which has checked hw > 0 once; the values
+// are those of the general form, which computes hw + 0 du + 0 dv.
+template <int DOMAIN, bool AFF = false>
 __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du, float dv, float gp, float cr,
-                                              float cg, float cb, Acc &a)
+                                              float cg, float cb, Acc &a, float r_aff = 0.f)
 {
-    const float Nw = fmaf(K.a20, du, fmaf(K.a21, dv, K.hw));     // camera-i depth * g.p
+    const float Nw = AFF ? K.hw : fmaf(K.a20, du, fmaf(K.a21, dv, K.hw));   // camera-i depth * g.p
     const float ex = fmaf(K.b0, du, fmaf(K.b1, dv, K.cx));
     const float ey = fmaf(K.c0, du, fmaf(K.c1, dv, K.cy));
-    const float r = rcp_approx(Nw);
-    sample_tail<DOMAIN>(K, act, Nw, fmaf(ex, r, ROUND_MAGIC), fmaf(ey, r, ROUND_MAGIC), gp, gp * r, cr, cg, cb, a);
+    const float r = AFF ? r_aff : rcp_approx(Nw);
+    sample_tail<DOMAIN, !AFF>(K, act, Nw, fmaf(ex, r, ROUND_MAGIC), fmaf(ey, r, ROUND_MAGIC), gp, gp * r, cr, cg,
+                              cb, a);
 }
 
 // The view terms V_i + O_i (Eq. 9-11) of every candidate of `mask` (a batch
@@ -395,7 +399,7 @@ __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du
 // terms of lfd_score to `rec`.  Lane c keeps candidate c's running sum in a
 // register (the reduced terms are identical in every lane), so the loop has
 // no divergent store.
-template <int DOMAIN, int SL, bool MASK_ALL = false, bool REC = false>
+template <int DOMAIN, int SL, bool MASK_ALL = false, bool REC = false, bool AFF = false>
 __device__ __noinline__ void view_terms(const Workspace &w, unsigned mask, float *rec)
 {
     const int lane = threadIdx.x & 31;
@@ -424,25 +428,32 @@ __device__ __noinline__ void view_terms(const Workspace &w, unsigned mask, float
             K.map = sv.map;
             K.xy = DOMAIN == 0 ? sh.xy_lo : sh.xy_hi;
             Acc a = {0u, 0u, 0u, 0.f, 0.f};
-            // slots j and j + 1 come from one shared-memory load; every slot
-            // but the last is full unless MASK_ALL
+            // affine pair: one reciprocal for every pixel; a plane behind
+            // camera i there (hw <= 0) has no valid pixel
+            const float r_aff = AFF ? rcp_approx(K.hw) : 0.f;
+            if (!AFF || K.hw > 0.f) {
+                // slots j and j + 1 come from one shared-memory load; every slot
+                // but the last is full unless MASK_ALL
 #pragma unroll
-            for (int jp = 0; jp < (SL + 1) / 2; jp++) {
-                const int j0 = 2 * jp, j1 = 2 * jp + 1;
-                const float4 d = sh.px4[32 * jp + lane];
-                energy_sample<DOMAIN>(K, (!MASK_ALL && j0 + 1 < SL) || lane + 32 * j0 < S.n, d.x, d.z,
-                                      fmaf(h.g0, d.x, fmaf(h.g1, d.z, h.gr)), S.cr, S.cg, S.cb, a);
-                if (j1 < SL)
-                    energy_sample<DOMAIN>(K, (!MASK_ALL && j1 + 1 < SL) || lane + 32 * j1 < S.n, d.y, d.w,
-                                          fmaf(h.g0, d.y, fmaf(h.g1, d.w, h.gr)), S.cr, S.cg, S.cb, a);
-            }
-            if (SL == SLOTS_MAX) {
+                for (int jp = 0; jp < (SL + 1) / 2; jp++) {
+                    const int j0 = 2 * jp, j1 = 2 * jp + 1;
+                    const float4 d = sh.px4[32 * jp + lane];
+                    energy_sample<DOMAIN, AFF>(K, (!MASK_ALL && j0 + 1 < SL) || lane + 32 * j0 < S.n, d.x, d.z,
+                                               fmaf(h.g0, d.x, fmaf(h.g1, d.z, h.gr)), S.cr, S.cg, S.cb, a, r_aff);
+                    if (j1 < SL)
+                        energy_sample<DOMAIN, AFF>(K, (!MASK_ALL && j1 + 1 < SL) || lane + 32 * j1 < S.n, d.y, d.w,
+                                                   fmaf(h.g0, d.y, fmaf(h.g1, d.w, h.gr)), S.cr, S.cg, S.cb, a,
+                                                   r_aff);
+                }
+                if (SL == SLOTS_MAX) {
 #pragma unroll 2
-                for (int i = 32 * SL + lane; i < S.n; i += 32) {    // pixels beyond the staged slots
-                    const unsigned pk = __ldg(w.sp_pix + S.off + i);
-                    const float du = (float)((int)(pk & 0xffff) - S.ref.x), dv = (float)((int)(pk >> 16) - S.ref.y);
-                    energy_sample<DOMAIN>(K, true, du, dv, fmaf(h.g0, du, fmaf(h.g1, dv, h.gr)), S.cr, S.cg, S.cb,
-                                          a);
+                    for (int i = 32 * SL + lane; i < S.n; i += 32) {    // pixels beyond the staged slots
+                        const unsigned pk = __ldg(w.sp_pix + S.off + i);
+                        const float du = (float)((int)(pk & 0xffff) - S.ref.x);
+                        const float dv = (float)((int)(pk >> 16) - S.ref.y);
+                        energy_sample<DOMAIN, AFF>(K, true, du, dv, fmaf(h.g0, du, fmaf(h.g1, dv, h.gr)), S.cr, S.cg,
+                                                   S.cb, a, r_aff);
+                    }
                 }
             }
             unsigned cnt, nx;
@@ -704,9 +715,9 @@ __device__ __forceinline__ int slot_class(int n)
 
 // one Jacobi update of superpixel gs by one warp (iteration `iter`, 1-based),
 // its pixels in SL slots per lane
-template <int DOMAIN, int SL>
+template <int DOMAIN, int SL, bool AFF>
 __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, const float4 *planes_in,
-                                          float4 *planes_out, int *choice, float *energy)
+                                          float4 *planes_out, int *choice, float *energy, int batch)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     SpShared &sh = g_sh[wid];
@@ -726,11 +737,13 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
     const int nr = w.radii_cnt[S.v * (LFD_MAX_ITER_INDEX + 1) + ii];
     const short *rad = w.radii + ((long long)S.v * (LFD_MAX_ITER_INDEX + 1) + ii) * LFD_MAX_RADII;
     const int M = 9 + 8 * nr;
-    for (int base = 0; base < M; base += 32) {
+    // candidates m = base .. base + batch - 1 (lane m - base), scored together
+    for (int base = 0; base < M; base += batch) {
         const int m = base + lane;
         bool ok = false;
         double g0 = 0.0, g1 = 0.0, igc = 0.0;
-        if (m == 0) {
+        if (lane >= batch) {
+        } else if (m == 0) {
             ok = gc.w != 0.0;
             g0 = gc.x; g1 = gc.y;
             igc = gc.x * sh.cx + gc.y * sh.cy + gc.z;
@@ -765,7 +778,7 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
         cs.ec[lane] = 0.f;
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         __syncwarp();
-        if (mask) view_terms<DOMAIN, SL>(w, mask, nullptr);
+        if (mask) view_terms<DOMAIN, SL, false, false, AFF>(w, mask, nullptr);
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
@@ -808,7 +821,7 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
         cs.ec[lane] = 0.f;
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         __syncwarp();
-        if (mask) view_terms<DOMAIN, SL>(w, mask, nullptr);
+        if (mask) view_terms<DOMAIN, SL, false, false, AFF>(w, mask, nullptr);
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
@@ -841,7 +854,7 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
 // set-up and slot-count dispatch of one superpixel; each slot count is a
 // separate (not inlined) function, so that every variant gets its own
 // register allocation
-template <int DOMAIN>
+template <int DOMAIN, bool AFF>
 __device__ __forceinline__ void propagate_one(const Workspace &w, const Consts &c, int iter, int gs, int lane,
                                               const float4 *planes_in, float4 *planes_out, int *choice,
                                               float *energy)
@@ -869,31 +882,31 @@ __device__ __forceinline__ void propagate_one(const Workspace &w, const Consts &
         return;
     }
     switch (slot_class(S.n)) {
-    case 1: propagate_sp<DOMAIN, 1>(w, iter, gs, planes_in, planes_out, choice, energy); break;
-    case 2: propagate_sp<DOMAIN, 2>(w, iter, gs, planes_in, planes_out, choice, energy); break;
-    case 3: propagate_sp<DOMAIN, 3>(w, iter, gs, planes_in, planes_out, choice, energy); break;
-    case 4: propagate_sp<DOMAIN, 4>(w, iter, gs, planes_in, planes_out, choice, energy); break;
-    case 5: propagate_sp<DOMAIN, 5>(w, iter, gs, planes_in, planes_out, choice, energy); break;
-    case 6: propagate_sp<DOMAIN, 6>(w, iter, gs, planes_in, planes_out, choice, energy); break;
-    case 7: propagate_sp<DOMAIN, 7>(w, iter, gs, planes_in, planes_out, choice, energy); break;
-    case 8: propagate_sp<DOMAIN, 8>(w, iter, gs, planes_in, planes_out, choice, energy); break;
-    default: propagate_sp<DOMAIN, SLOTS_MAX>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 1: propagate_sp<DOMAIN, 1, AFF>(w, iter, gs, planes_in, planes_out, choice, energy, c.cand_batch); break;
+    case 2: propagate_sp<DOMAIN, 2, AFF>(w, iter, gs, planes_in, planes_out, choice, energy, c.cand_batch); break;
+    case 3: propagate_sp<DOMAIN, 3, AFF>(w, iter, gs, planes_in, planes_out, choice, energy, c.cand_batch); break;
+    case 4: propagate_sp<DOMAIN, 4, AFF>(w, iter, gs, planes_in, planes_out, choice, energy, c.cand_batch); break;
+    case 5: propagate_sp<DOMAIN, 5, AFF>(w, iter, gs, planes_in, planes_out, choice, energy, c.cand_batch); break;
+    case 6: propagate_sp<DOMAIN, 6, AFF>(w, iter, gs, planes_in, planes_out, choice, energy, c.cand_batch); break;
+    case 7: propagate_sp<DOMAIN, 7, AFF>(w, iter, gs, planes_in, planes_out, choice, energy, c.cand_batch); break;
+    case 8: propagate_sp<DOMAIN, 8, AFF>(w, iter, gs, planes_in, planes_out, choice, energy, c.cand_batch); break;
+    default: propagate_sp<DOMAIN, SLOTS_MAX, AFF>(w, iter, gs, planes_in, planes_out, choice, energy, c.cand_batch); break;
     }
 }
 
-template <int DOMAIN, int MINB>
+template <int DOMAIN, int MINB, bool AFF>
 __global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate(const __grid_constant__ Workspace w, Consts c, int iter,
                                                                      const float4 *planes_in, float4 *planes_out,
                                                                      int *choice, float *energy)
 {
     const int item = blockIdx.x * PROP_WARPS + (threadIdx.x >> 5);
     if (item >= w.S_total) return;
-    propagate_one<DOMAIN>(w, c, iter, __ldg(w.order + item), threadIdx.x & 31, planes_in, planes_out, choice,
-                          energy);
+    propagate_one<DOMAIN, AFF>(w, c, iter, __ldg(w.order + item), threadIdx.x & 31, planes_in, planes_out, choice,
+                               energy);
 }
 
 // persistent warps: superpixels taken from the cost-ordered queue, most expensive first
-template <int DOMAIN, int MINB>
+template <int DOMAIN, int MINB, bool AFF>
 __global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate_persistent(const __grid_constant__ Workspace w, Consts c, int iter,
                                                                                 const float4 *planes_in,
                                                                                 float4 *planes_out, int *choice,
@@ -905,43 +918,55 @@ __global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate_persistent(
         if (lane == 0) item = atomicAdd(&w.queue[1], 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= w.S_total) break;
-        propagate_one<DOMAIN>(w, c, iter, __ldg(w.order + item), lane, planes_in, planes_out, choice, energy);
+        propagate_one<DOMAIN, AFF>(w, c, iter, __ldg(w.order + item), lane, planes_in, planes_out, choice, energy);
         __syncwarp();
     }
 }
 
-template <int DOMAIN, int MINB>
+template <int DOMAIN, int MINB, bool AFF>
 static cudaError_t launch_propagate_t(const Workspace &w, const Consts &c, const LaunchCfg &lc, int iter,
                                       const float4 *planes_in, float4 *planes_out, int *choice, float *energy,
                                       cudaStream_t st)
 {
     if (lc.prop_persistent) {
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate_persistent<DOMAIN, MINB>,
-                                                                      32 * PROP_WARPS, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_propagate_persistent<DOMAIN, MINB, AFF>, 32 * PROP_WARPS, 0);
         if (e != cudaSuccess) return e;
         const int warps = (w.S_total + PROP_WARPS - 1) / PROP_WARPS;
         const int grid = max(1, min(warps, per_sm * lc.num_sms));
-        k_propagate_persistent<DOMAIN, MINB><<<grid, 32 * PROP_WARPS, 0, st>>>(w, c, iter, planes_in, planes_out,
-                                                                               choice, energy);
+        k_propagate_persistent<DOMAIN, MINB, AFF><<<grid, 32 * PROP_WARPS, 0, st>>>(w, c, iter, planes_in,
+                                                                                    planes_out, choice, energy);
     } else {
         const int blocks = (w.S_total + PROP_WARPS - 1) / PROP_WARPS;
-        k_propagate<DOMAIN, MINB><<<blocks, 32 * PROP_WARPS, 0, st>>>(w, c, iter, planes_in, planes_out, choice,
-                                                                      energy);
+        k_propagate<DOMAIN, MINB, AFF><<<blocks, 32 * PROP_WARPS, 0, st>>>(w, c, iter, planes_in, planes_out, choice,
+                                                                           energy);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_propagate(const Workspace &w, const Consts &c, const LaunchCfg &lc, int iter,
+template <int DOMAIN, int MINB>
+static cudaError_t launch_propagate_m(const Workspace &w, const Consts &c, const LaunchCfg &lc, int iter,
+                                      const float4 *planes_in, float4 *planes_out, int *choice, float *energy,
+                                      cudaStream_t st)
+{
+    return c.affine ? launch_propagate_t<DOMAIN, MINB, true>(w, c, lc, iter, planes_in, planes_out, choice, energy, st)
+                    : launch_propagate_t<DOMAIN, MINB, false>(w, c, lc, iter, planes_in, planes_out, choice, energy,
+                                                              st);
+}
+
+cudaError_t launch_propagate(const Workspace &w, const Consts &c0, const LaunchCfg &lc, int iter,
                              const float4 *planes_in, float4 *planes_out, int *choice, float *energy,
                              cudaStream_t st)
 {
+    Consts c = c0;
+    c.cand_batch = lc.prop_batch == 16 ? 16 : 32;
     const bool eight = lc.prop_blocks >= 8;
     if (c.domain == 0)
-        return eight ? launch_propagate_t<0, 8>(w, c, lc, iter, planes_in, planes_out, choice, energy, st)
-                     : launch_propagate_t<0, 7>(w, c, lc, iter, planes_in, planes_out, choice, energy, st);
-    return eight ? launch_propagate_t<1, 8>(w, c, lc, iter, planes_in, planes_out, choice, energy, st)
-                 : launch_propagate_t<1, 7>(w, c, lc, iter, planes_in, planes_out, choice, energy, st);
+        return eight ? launch_propagate_m<0, 8>(w, c, lc, iter, planes_in, planes_out, choice, energy, st)
+                     : launch_propagate_m<0, 7>(w, c, lc, iter, planes_in, planes_out, choice, energy, st);
+    return eight ? launch_propagate_m<1, 8>(w, c, lc, iter, planes_in, planes_out, choice, energy, st)
+                 : launch_propagate_m<1, 7>(w, c, lc, iter, planes_in, planes_out, choice, energy, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -376,30 +376,31 @@ cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStr
 //    and read 6x more DRAM).  Deterministic.
 // ---------------------------------------------------------------------------
 
-//    Inside a class the superpixels go by row band (ORDER_BANDS bands of
-//    each view's grid rows) and then in index order: the superpixels in
+//    Inside a class the superpixels go by row band (up to ORDER_BANDS
+//    bands of each view's grid rows, a launch-shape option) and then in
+//    index order: the superpixels in
 //    flight at any time cover the same rows of every view, so the rows of
 //    the sampling textures and rasterised maps they gather from (their own
 //    band, shifted by the disparity, in each neighbour view) stay in L2
 //    together instead of spanning whole views.
 
-__device__ __forceinline__ int order_key(const Workspace &w, int gs, int mode)
+__device__ __forceinline__ int order_key(const Workspace &w, int gs, int mode, int bands)
 {
     const int n = __ldg(w.sp_cnt + gs);
     const int cls = mode == 0 ? (n + 31) >> 5 : 31 - __clz(max(n, 1));
     const ViewDev &vd = w.views[__ldg(w.sp_view + gs)];
     const int gy = (gs - vd.sp_base) / vd.GW;
-    const int band = min(ORDER_BANDS - 1, (int)(((long long)gy * ORDER_BANDS) / vd.GH));
+    const int band = min(bands - 1, (int)(((long long)gy * bands) / vd.GH));
     return (ORDER_CLASSES - 1 - min(cls, ORDER_CLASSES - 1)) * ORDER_BANDS + band;   // 0 = largest class, top band
 }
 
-__global__ void k_order_hist(Workspace w, int *hist, int mode)
+__global__ void k_order_hist(Workspace w, int *hist, int mode, int bands)
 {
     __shared__ int h[ORDER_KEYS];
     for (int k = threadIdx.x; k < ORDER_KEYS; k += blockDim.x) h[k] = 0;
     __syncthreads();
     const int gs = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gs < w.S_total) atomicAdd(&h[order_key(w, gs, mode)], 1);
+    if (gs < w.S_total) atomicAdd(&h[order_key(w, gs, mode, bands)], 1);
     __syncthreads();
     for (int k = threadIdx.x; k < ORDER_KEYS; k += blockDim.x)
         if (h[k]) atomicAdd(&hist[k], h[k]);
@@ -407,7 +408,7 @@ __global__ void k_order_hist(Workspace w, int *hist, int mode)
 
 // one CTA of 1024 threads walks the superpixels in tiles of 1024; a
 // superpixel's slot is its key's start + the count of equal keys before it
-__global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *hist, int *order, int mode)
+__global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *hist, int *order, int mode, int bands)
 {
     __shared__ int run[ORDER_KEYS];                  // running position per key
     __shared__ int wcnt[32][ORDER_KEYS];             // per-warp counts of the tile
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *
         __syncthreads();
         const int gs = base + t;
         const bool in = gs < w.S_total;
-        const int key = in ? order_key(w, gs, mode) : ORDER_KEYS;    // out-of-range lanes use a key of their own
+        const int key = in ? order_key(w, gs, mode, bands) : ORDER_KEYS;   // out-of-range lanes: a key of their own
         const unsigned same = __match_any_sync(0xffffffffu, key);
         const int rank = __popc(same & ((1u << lane) - 1u));
         if (in && rank == 0) wcnt[wid][key] = __popc(same);
@@ -444,13 +445,14 @@ __global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *
     }
 }
 
-cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, cudaStream_t st)
+cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, int bands, cudaStream_t st)
 {
+    bands = max(1, min(bands, ORDER_BANDS));
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * ORDER_KEYS, st);
     if (e != cudaSuccess) return e;
     const int blocks = (w.S_total + 255) / 256;
-    k_order_hist<<<blocks, 256, 0, st>>>(w, hist, mode);
-    k_order_scatter<<<1, 1024, 0, st>>>(w, hist, order, mode);
+    k_order_hist<<<blocks, 256, 0, st>>>(w, hist, mode, bands);
+    k_order_scatter<<<1, 1024, 0, st>>>(w, hist, order, mode, bands);
     return cudaGetLastError();
 }
 

@@ -52,7 +52,7 @@ struct SweepShared {
 };
 
 // the whole sweep of superpixel gs by one CTA (threads = labels)
-template <int FMT, bool WORLD, int THREADS>
+template <int FMT, bool WORLD, int THREADS, bool AFF>
 __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, int gs, SweepShared<THREADS, WORLD> &sh,
                                          float4 *planes, int *label_out, float *cost_out)
 {
@@ -177,6 +177,23 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
                         if (rc.w == 0.f) t = T;
                         cost += t;
                     }
+                } else if (AFF) {
+                    // affine pair: the homogeneous coordinate is cw for every pixel
+                    // (P row 3 = (0, 0, P22), q_z = 0), one reciprocal per label and view;
+                    // the same arithmetic as the general loop, value for value
+                    const float4 *xyw = sh.xyw[WORLD ? 0 : j];
+                    const float rw = rcp_approx(cw);
+                    if (cw > 0.f) {
+#pragma unroll 4
+                        for (int i = 0; i < cn; i++) {
+                            const float4 q = xyw[i];
+                            const float4 rc = sh.ref[i];
+                            cost += tssd_at<FMT>(tex, Wi, Hi, (q.x + cx) * rw, (q.y + cy) * rw,
+                                                 make_float3(rc.x, rc.y, rc.z), T);
+                        }
+                    } else {
+                        for (int i = 0; i < cn; i++) cost += T;
+                    }
                 } else {
                     const float4 *xyw = sh.xyw[WORLD ? 0 : j];
 #pragma unroll 4
@@ -233,17 +250,19 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
 }
 
 // one CTA per superpixel
-template <int FMT, bool WORLD, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_sweep(Workspace w, Consts c, float4 *planes, int *label_out,
+// camera-frame sweeps: 6 CTAs of 256 threads (12 of 128) per SM, at most 40 registers;
+// world-frame sweeps (more FP64 per label) 4, at most 64
+template <int FMT, bool WORLD, int THREADS, bool AFF>
+__global__ void __launch_bounds__(THREADS, (WORLD ? 1024 : 1536) / THREADS) k_sweep(Workspace w, Consts c, float4 *planes, int *label_out,
                                                    float *cost_out)
 {
     __shared__ SweepShared<THREADS, WORLD> sh;
-    sweep_sp<FMT, WORLD, THREADS>(w, c, blockIdx.x, sh, planes, label_out, cost_out);
+    sweep_sp<FMT, WORLD, THREADS, AFF>(w, c, blockIdx.x, sh, planes, label_out, cost_out);
 }
 
 // persistent CTAs: superpixels taken from the size-ordered queue, largest class first
-template <int FMT, bool WORLD, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_sweep_persistent(Workspace w, Consts c, float4 *planes, int *label_out,
+template <int FMT, bool WORLD, int THREADS, bool AFF>
+__global__ void __launch_bounds__(THREADS, (WORLD ? 1024 : 1536) / THREADS) k_sweep_persistent(Workspace w, Consts c, float4 *planes, int *label_out,
                                                               float *cost_out)
 {
     __shared__ SweepShared<THREADS, WORLD> sh;
@@ -253,26 +272,34 @@ __global__ void __launch_bounds__(THREADS) k_sweep_persistent(Workspace w, Const
         const int item = sh.item;
         __syncthreads();
         if (item >= w.S_total) break;
-        sweep_sp<FMT, WORLD, THREADS>(w, c, __ldg(w.order_sweep + item), sh, planes, label_out, cost_out);
+        sweep_sp<FMT, WORLD, THREADS, AFF>(w, c, __ldg(w.order_sweep + item), sh, planes, label_out, cost_out);
         __syncthreads();
     }
+}
+
+template <int FMT, bool WORLD, int THREADS, bool AFF>
+static cudaError_t launch_sweep_a(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
+                                  float *cost, cudaStream_t st)
+{
+    if (lc.sweep_persistent) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_sweep_persistent<FMT, WORLD, THREADS, AFF>, THREADS, 0);
+        if (e != cudaSuccess) return e;
+        const int grid = max(1, min(w.S_total, per_sm * lc.num_sms));
+        k_sweep_persistent<FMT, WORLD, THREADS, AFF><<<grid, THREADS, 0, st>>>(w, c, planes, label, cost);
+    } else {
+        k_sweep<FMT, WORLD, THREADS, AFF><<<w.S_total, THREADS, 0, st>>>(w, c, planes, label, cost);
+    }
+    return cudaGetLastError();
 }
 
 template <int FMT, bool WORLD, int THREADS>
 static cudaError_t launch_sweep_t(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
                                   float *cost, cudaStream_t st)
 {
-    if (lc.sweep_persistent) {
-        int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_persistent<FMT, WORLD, THREADS>,
-                                                                      THREADS, 0);
-        if (e != cudaSuccess) return e;
-        const int grid = max(1, min(w.S_total, per_sm * lc.num_sms));
-        k_sweep_persistent<FMT, WORLD, THREADS><<<grid, THREADS, 0, st>>>(w, c, planes, label, cost);
-    } else {
-        k_sweep<FMT, WORLD, THREADS><<<w.S_total, THREADS, 0, st>>>(w, c, planes, label, cost);
-    }
-    return cudaGetLastError();
+    if (!WORLD && c.affine) return launch_sweep_a<FMT, false, THREADS, true>(w, c, lc, planes, label, cost, st);
+    return launch_sweep_a<FMT, WORLD, THREADS, false>(w, c, lc, planes, label, cost, st);
 }
 
 template <int FMT>

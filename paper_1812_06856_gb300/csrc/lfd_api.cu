@@ -183,7 +183,7 @@ struct lfd_ctx {
     std::vector<LfInfo> lfs;
     std::vector<int> nbr;          // [V_total * 8] global view indices
     int fmt = 0;
-    LaunchCfg lc{256, 1, 8, 1, 0};
+    LaunchCfg lc{256, 1, 8, 1, 0, 32, ORDER_BANDS};
     // workspace
     Arena ws;
     Workspace w{};
@@ -688,6 +688,17 @@ lfd_status plan_input(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, const lfd_
             }
         }
     }
+    // affine pairs: P row 3 = (0, 0, P22) and q_z = 0, so A(g) = P + q g^T keeps
+    // row 3 = (0, 0, P22) for every plane g (cameras with parallel optical axes
+    // and equal z in the reference frame, e.g. planar arrays)
+    int affine = 1;
+    for (int v = 0; v < V; v++)
+        for (int k = 0; k < LFD_MAXN; k++) {
+            if (ctx->nbr[(size_t)v * LFD_MAXN + k] < 0) continue;
+            const PairDev &pd = hp[v * LFD_MAXN + k];
+            if (pd.P[6] != 0.0 || pd.P[7] != 0.0 || pd.q[2] != 0.0) affine = 0;
+        }
+    ctx->c.affine = affine;
     return LFD_OK;
 }
 
@@ -722,10 +733,12 @@ lfd_status enqueue_input(lfd_ctx *ctx, cudaStream_t st, bool record_event)
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_quads(ctx->w, V, max_quads, ctx->fmt, st); }));
     // work orders: propagation by descending slot class, the sweep by descending
     // power-of-two size class, index order inside a class
-    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st,
-                    [&] { return launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, 0, st); }, 2));
-    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st,
-                    [&] { return launch_sp_order(ctx->w, ctx->d_order_sweep, ctx->d_hist, 1, st); }, 2));
+    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
+        return launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, 0, ctx->lc.order_bands, st);
+    }, 2));
+    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
+        return launch_sp_order(ctx->w, ctx->d_order_sweep, ctx->d_hist, 1, ctx->lc.order_bands, st);
+    }, 2));
     return LFD_OK;
 }
 
@@ -867,6 +880,10 @@ lfd_status enqueue_frame(lfd_ctx *ctx, const float *const *warm, float *const *c
 
 // Launch-shape autotuner: times each sweep and propagate variant on the bound
 // input (one warm-up run, then the median of three) and keeps the fastest.
+// Axes: sweep threads 128/256 x grid/persistent x row bands 1/16 of the
+// sweep's work order; propagation CTAs per SM 7/8 x grid/persistent x
+// candidates per pass 16/32 x row bands 1/16 (iteration 1, the widest kernel).
+// Results do not depend on the shape (per-superpixel work is the same).
 lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
 {
     const bool prof = ctx->prof;
@@ -889,47 +906,70 @@ lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
         ms = t[1];
         return LFD_OK;
     };
+    auto order = [&](int mode, int bands) -> lfd_status {
+        LFD_CUDA(launch_sp_order(ctx->w, mode == 0 ? ctx->d_order : ctx->d_order_sweep, ctx->d_hist, mode, bands, st));
+        return LFD_OK;
+    };
     lfd_status s;
     LaunchCfg best = ctx->lc;
     float best_ms = 1e30f;
-    const int th[2] = {128, 256};
-    for (int pi = 0; pi < 2; pi++)
-        for (int ti = 0; ti < 2; ti++) {
-            ctx->lc.sweep_threads = th[ti];
-            ctx->lc.sweep_persistent = pi;
-            float ms = 0;
-            if ((s = time_it([&] { return run_sweep(ctx, nullptr, st); }, ms)) != LFD_OK) return s;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best.sweep_threads = th[ti];
-                best.sweep_persistent = pi;
+    const int th[2] = {128, 256}, bands[2] = {1, ORDER_BANDS};
+    int sweep_bands = ORDER_BANDS, prop_bands = ORDER_BANDS;
+    for (int bi = 0; bi < 2; bi++) {
+        if ((s = order(1, bands[bi])) != LFD_OK) return s;
+        for (int pi = 0; pi < 2; pi++)
+            for (int ti = 0; ti < 2; ti++) {
+                ctx->lc.sweep_threads = th[ti];
+                ctx->lc.sweep_persistent = pi;
+                float ms = 0;
+                if ((s = time_it([&] { return run_sweep(ctx, nullptr, st); }, ms)) != LFD_OK) return s;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best.sweep_threads = th[ti];
+                    best.sweep_persistent = pi;
+                    sweep_bands = bands[bi];
+                }
             }
-        }
+    }
     ctx->lc.sweep_threads = best.sweep_threads;
     ctx->lc.sweep_persistent = best.sweep_persistent;
+    if ((s = order(1, sweep_bands)) != LFD_OK) return s;
     if ((s = run_sweep(ctx, nullptr, st)) != LFD_OK) return s;
     if ((s = rasterize_state(ctx, ctx->d_planesA, nullptr, st)) != LFD_OK) return s;
     best_ms = 1e30f;
-    const int pb[2] = {7, 8};
-    for (int pi = 0; pi < 2; pi++)
-        for (int bi = 0; bi < 2; bi++) {
-            ctx->lc.prop_blocks = pb[bi];
-            ctx->lc.prop_persistent = pi;
-            float ms = 0;
-            auto fn = [&]() -> lfd_status {
-                if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 16, st));
-                LFD_CUDA(launch_propagate(ctx->w, ctx->c, ctx->lc, 1, ctx->d_planesA, ctx->d_planesB, nullptr, nullptr,
-                                          st));
-                return LFD_OK;
-            };
-            if ((s = time_it(fn, ms)) != LFD_OK) return s;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best.prop_blocks = pb[bi];
-                best.prop_persistent = pi;
-            }
-        }
+    const int pb[2] = {7, 8}, cb[2] = {16, 32};
+    for (int bi = 0; bi < 2; bi++) {
+        if ((s = order(0, bands[bi])) != LFD_OK) return s;
+        for (int pi = 0; pi < 2; pi++)
+            for (int ki = 0; ki < 2; ki++)
+                for (int ci = 0; ci < 2; ci++) {
+                    ctx->lc.prop_blocks = pb[ki];
+                    ctx->lc.prop_persistent = pi;
+                    ctx->lc.prop_batch = cb[ci];
+                    float ms = 0;
+                    auto fn = [&]() -> lfd_status {
+                        if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 16, st));
+                        LFD_CUDA(launch_propagate(ctx->w, ctx->c, ctx->lc, 1, ctx->d_planesA, ctx->d_planesB, nullptr,
+                                                  nullptr, st));
+                        return LFD_OK;
+                    };
+                    if ((s = time_it(fn, ms)) != LFD_OK) return s;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best.prop_blocks = pb[ki];
+                        best.prop_persistent = pi;
+                        best.prop_batch = cb[ci];
+                        prop_bands = bands[bi];
+                    }
+                }
+    }
+    // one band count serves both orders (enqueue_input builds both with it):
+    // the propagation's choice, the larger share of a frame's time
+    best.order_bands = prop_bands;
     ctx->lc = best;
+    if ((s = order(0, prop_bands)) != LFD_OK) return s;
+    if ((s = order(1, prop_bands)) != LFD_OK) return s;
+    (void)sweep_bands;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->prof = prof;
@@ -990,13 +1030,18 @@ lfd_status apply_options(lfd_ctx *ctx, const lfd_batch_options &o)
 {
     if ((o.sweep_threads != 0 && o.sweep_threads != 128 && o.sweep_threads != 256) ||
         (o.prop_blocks != 0 && o.prop_blocks != 7 && o.prop_blocks != 8) || (o.sweep_persistent & ~1) ||
-        (o.prop_persistent & ~1) || (o.autotune & ~1) || (o.graph & ~1))
-        return fail(ctx, LFD_ERR_INVALID_ARG, "batch options: sweep_threads 0/128/256, prop_blocks 0/7/8, flags 0/1");
+        (o.prop_persistent & ~1) || (o.autotune & ~1) || (o.graph & ~1) ||
+        (o.prop_batch != 0 && o.prop_batch != 16 && o.prop_batch != 32) ||
+        (o.order_bands != 0 && o.order_bands != 1 && o.order_bands != ORDER_BANDS))
+        return fail(ctx, LFD_ERR_INVALID_ARG, "batch options: sweep_threads 0/128/256, prop_blocks 0/7/8, "
+                                              "prop_batch 0/16/32, order_bands 0/1/16, flags 0/1");
     if (o.autotune) return LFD_OK;
     ctx->lc.sweep_threads = o.sweep_threads ? o.sweep_threads : 256;
     ctx->lc.sweep_persistent = o.sweep_persistent;
     ctx->lc.prop_blocks = o.prop_blocks ? o.prop_blocks : 8;
     ctx->lc.prop_persistent = o.prop_persistent;
+    ctx->lc.prop_batch = o.prop_batch ? o.prop_batch : 32;
+    ctx->lc.order_bands = o.order_bands ? o.order_bands : ORDER_BANDS;
     return LFD_OK;
 }
 
@@ -1072,6 +1117,8 @@ void lfd_batch_options_default(lfd_batch_options *o)
     o->sweep_persistent = 1;
     o->prop_blocks = 8;
     o->prop_persistent = 1;
+    o->prop_batch = 32;
+    o->order_bands = ORDER_BANDS;
 }
 
 lfd_status lfd_create(lfd_ctx **out, int32_t device, uint64_t hbm_budget_bytes)
@@ -1642,6 +1689,8 @@ lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out)
     out[1] = ctx->lc.sweep_persistent;
     out[2] = ctx->lc.prop_blocks;
     out[3] = ctx->lc.prop_persistent;
+    out[4] = ctx->lc.prop_batch;
+    out[5] = ctx->lc.order_bands;
     return LFD_OK;
 }
 lfd_status lfd_synchronize(lfd_ctx *ctx, void *stream)

@@ -89,7 +89,10 @@ struct Consts {
     int sweep_frame;
     int batch_iters;         // 1: a view whose light field has run its iterations passes its plane through
     float col_scale;         // sampler colour units -> [0,1]
-    float pad1;
+    int cand_batch;          // candidate planes per pass (16 or 32; LaunchCfg::prop_batch)
+    int affine;              // 1: every pair's homography has third row (0, 0, c) for every plane
+                             //    (parallel cameras, common principal depth axis): the sample's depth
+                             //    term is constant per (hypothesis, view) and the kernels skip it
 };
 
 struct Workspace {
@@ -246,6 +249,8 @@ struct LaunchCfg {
     int prop_blocks;         // 7 or 8 resident 4-warp CTAs per SM (register budget)
     int prop_persistent;     // 1: persistent warps over a cost-ordered queue
     int num_sms;
+    int prop_batch;          // 16 or 32 candidate planes per pass over the neighbour views
+    int order_bands;         // 1 or 16 row bands in the work orders
 };
 
 cudaError_t launch_sp_count(const Workspace &w, int V, int max_px, int *cnt, int4 *bbox, cudaStream_t st);
@@ -259,7 +264,9 @@ cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStr
 constexpr int ORDER_CLASSES = 17;
 constexpr int ORDER_BANDS = 16;
 constexpr int ORDER_KEYS = ORDER_CLASSES * ORDER_BANDS;
-cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, cudaStream_t st);  // hist: ORDER_KEYS ints
+// bands: 1 .. ORDER_BANDS row bands inside a size class
+cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, int bands,
+                            cudaStream_t st);  // hist: ORDER_KEYS ints
 cudaError_t launch_sweep(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
                          float *cost, cudaStream_t st);
 cudaError_t launch_plane_prep(const Workspace &w, const Consts &c, const float4 *planes, double4_32a *g, float4 *rc,

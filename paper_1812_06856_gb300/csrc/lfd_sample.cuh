@@ -123,13 +123,12 @@ __device__ __forceinline__ float3 texel_colour(const void *tex, int x, int y, in
 // camera i (Wz <= 0) or off the image's texture area -1/2 <= x < Wi - 1/2,
 // -1/2 <= y < Hi - 1/2 (its nearest pixel is not a pixel of view i).  Inside,
 // the texture's border quads give clamp-to-edge (see k_quads).
+// tssd_at: the same at the dehomogenised point (x, y) of a point in front of
+// camera i.
 template <int FMT>
-__device__ __forceinline__ float tssd_sample(const void *tex, int Wi, int Hi, float X, float Y, float Wz, float3 ref,
-                                             float T)
+__device__ __forceinline__ float tssd_at(const void *tex, int Wi, int Hi, float x, float y, float3 ref, float T)
 {
-    const float rw = rcp_approx(Wz);
-    const float x = X * rw, y = Y * rw;
-    const bool ok = (Wz > 0.f) && (x >= -0.5f) && (x < (float)Wi - 0.5f) && (y >= -0.5f) && (y < (float)Hi - 0.5f);
+    const bool ok = (x >= -0.5f) && (x < (float)Wi - 0.5f) && (y >= -0.5f) && (y < (float)Hi - 0.5f);
     if (!ok) return T;
     const float xf = floorf(x), yf = floorf(y);          // -1 .. W-1, -1 .. H-1
     const float fx = x - xf, fy = y - yf;
@@ -157,6 +156,15 @@ __device__ __forceinline__ float tssd_sample(const void *tex, int Wi, int Hi, fl
         const float db = ref.z - fmaf(fy, b1 - b0, b0);
         return fminf(fmaf(db, db, d2.x + d2.y), T);
     }
+}
+
+template <int FMT>
+__device__ __forceinline__ float tssd_sample(const void *tex, int Wi, int Hi, float X, float Y, float Wz, float3 ref,
+                                             float T)
+{
+    const float rw = rcp_approx(Wz);
+    if (!(Wz > 0.f)) return T;
+    return tssd_at<FMT>(tex, Wi, Hi, X * rw, Y * rw, ref, T);
 }
 
 }  // namespace lfd

@@ -61,7 +61,7 @@ class Query(C.Structure):
 class BatchOptions(C.Structure):
     _fields_ = [("autotune", C.c_int32), ("graph", C.c_int32), ("sweep_threads", C.c_int32),
                 ("sweep_persistent", C.c_int32), ("prop_blocks", C.c_int32), ("prop_persistent", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("prop_batch", C.c_int32), ("order_bands", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -531,9 +531,10 @@ class Context:
         return (labels, cout) if want_centres else labels
 
     def launch_config(self) -> dict:
-        out = (C.c_int32 * 4)()
+        out = (C.c_int32 * 6)()
         self._check(self.lib.lfd_launch_config(self.h, out), "lfd_launch_config")
-        return dict(sweep_threads=out[0], sweep_persistent=out[1], prop_blocks=out[2], prop_persistent=out[3])
+        return dict(sweep_threads=out[0], sweep_persistent=out[1], prop_blocks=out[2], prop_persistent=out[3],
+                    prop_batch=out[4], order_bands=out[5])
 
     def synchronize(self, stream=None):
         self._check(self.lib.lfd_synchronize(self.h, _stream(stream)), "lfd_synchronize")

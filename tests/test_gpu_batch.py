@@ -79,6 +79,9 @@ def test_batch_equals_separate_calls(lfd, two_rigs):
     dict(prop_blocks=7),
     dict(prop_persistent=0),
     dict(sweep_threads=128, sweep_persistent=1, prop_blocks=7, prop_persistent=1),
+    dict(prop_batch=16),
+    dict(order_bands=1),
+    dict(prop_batch=16, order_bands=1, prop_persistent=0),
 ])
 def test_launch_shapes_give_identical_bits(lfd, two_rigs, opt):
     ctx = lfd.Context(0)
@@ -106,6 +109,7 @@ def test_autotune_picks_a_valid_shape_and_same_bits(lfd, two_rigs):
     cfg = ctx2.launch_config()
     assert cfg["sweep_threads"] in (128, 256) and cfg["prop_blocks"] in (7, 8)
     assert cfg["sweep_persistent"] in (0, 1) and cfg["prop_persistent"] in (0, 1)
+    assert cfg["prop_batch"] in (16, 32) and cfg["order_bands"] in (1, 16)
     assert torch.equal(p0, p1)
     # counters count the frame only, not the timing runs
     h, s = ctx2.counters()
@@ -158,3 +162,5 @@ def test_batch_rejects_mixed_formats_and_graph_on_default_stream(lfd, two_rigs):
                            stream=torch.cuda.default_stream())
     with pytest.raises(lfd.LfdError, match="batch options"):
         ctx.estimate_batch([_item(a, va, la, pa)], options=dict(sweep_threads=64))
+    with pytest.raises(lfd.LfdError, match="batch options"):
+        ctx.estimate_batch([_item(a, va, la, pa)], options=dict(prop_batch=24))
