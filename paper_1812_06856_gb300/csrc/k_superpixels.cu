@@ -378,14 +378,17 @@ cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStr
 
 //    Inside a class the superpixels go by row band (up to ORDER_BANDS
 //    bands of each view's grid rows, a launch-shape option) and then in
-//    index order: the superpixels in
-//    flight at any time cover the same rows of every view, so the rows of
-//    the sampling textures and rasterised maps they gather from (their own
-//    band, shifted by the disparity, in each neighbour view) stay in L2
-//    together instead of spanning whole views.
+//    index order: the superpixels in flight at any time cover the same rows
+//    of every view, so the rows of the sampling textures and rasterised maps
+//    they gather from (their own band, shifted by the disparity, in each
+//    neighbour view) stay in L2 together instead of spanning whole views.
+//    The sweep's order is finally partitioned, stably, by the label-count
+//    class of each superpixel's light field (mode 2): one sweep launch per
+//    class, its CTAs as wide as the class's label count.
 
 __device__ __forceinline__ int order_key(const Workspace &w, int gs, int mode, int bands)
 {
+    if (mode == 2) return w.views[__ldg(w.sp_view + gs)].lclass;
     const int n = __ldg(w.sp_cnt + gs);
     const int cls = mode == 0 ? (n + 31) >> 5 : 31 - __clz(max(n, 1));
     const ViewDev &vd = w.views[__ldg(w.sp_view + gs)];
@@ -394,13 +397,13 @@ __device__ __forceinline__ int order_key(const Workspace &w, int gs, int mode, i
     return (ORDER_CLASSES - 1 - min(cls, ORDER_CLASSES - 1)) * ORDER_BANDS + band;   // 0 = largest class, top band
 }
 
-__global__ void k_order_hist(Workspace w, int *hist, int mode, int bands)
+__global__ void k_order_hist(Workspace w, int *hist, int mode, int bands, const int *in)
 {
     __shared__ int h[ORDER_KEYS];
     for (int k = threadIdx.x; k < ORDER_KEYS; k += blockDim.x) h[k] = 0;
     __syncthreads();
-    const int gs = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gs < w.S_total) atomicAdd(&h[order_key(w, gs, mode, bands)], 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < w.S_total) atomicAdd(&h[order_key(w, in ? __ldg(in + i) : i, mode, bands)], 1);
     __syncthreads();
     for (int k = threadIdx.x; k < ORDER_KEYS; k += blockDim.x)
         if (h[k]) atomicAdd(&hist[k], h[k]);
@@ -408,7 +411,8 @@ __global__ void k_order_hist(Workspace w, int *hist, int mode, int bands)
 
 // one CTA of 1024 threads walks the superpixels in tiles of 1024; a
 // superpixel's slot is its key's start + the count of equal keys before it
-__global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *hist, int *order, int mode, int bands)
+__global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *hist, int *order, int mode, int bands,
+                                                        const int *in)
 {
     __shared__ int run[ORDER_KEYS];                  // running position per key
     __shared__ int wcnt[32][ORDER_KEYS];             // per-warp counts of the tile
@@ -423,14 +427,15 @@ __global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *
     for (int base = 0; base < w.S_total; base += 1024) {
         for (int i = t; i < 32 * ORDER_KEYS; i += 1024) wcnt[i / ORDER_KEYS][i % ORDER_KEYS] = 0;
         __syncthreads();
-        const int gs = base + t;
-        const bool in = gs < w.S_total;
-        const int key = in ? order_key(w, gs, mode, bands) : ORDER_KEYS;   // out-of-range lanes: a key of their own
+        const int pos = base + t;
+        const bool ok = pos < w.S_total;
+        const int gs = ok ? (in ? __ldg(in + pos) : pos) : 0;
+        const int key = ok ? order_key(w, gs, mode, bands) : ORDER_KEYS;   // out-of-range lanes: a key of their own
         const unsigned same = __match_any_sync(0xffffffffu, key);
         const int rank = __popc(same & ((1u << lane) - 1u));
-        if (in && rank == 0) wcnt[wid][key] = __popc(same);
+        if (ok && rank == 0) wcnt[wid][key] = __popc(same);
         __syncthreads();
-        if (in) {
+        if (ok) {
             int before = 0;
             for (int u = 0; u < wid; u++) before += wcnt[u][key];
             order[run[key] + before + rank] = gs;
@@ -445,14 +450,15 @@ __global__ void __launch_bounds__(1024) k_order_scatter(Workspace w, const int *
     }
 }
 
-cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, int bands, cudaStream_t st)
+cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, int bands, const int *in,
+                            cudaStream_t st)
 {
     bands = max(1, min(bands, ORDER_BANDS));
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * ORDER_KEYS, st);
     if (e != cudaSuccess) return e;
     const int blocks = (w.S_total + 255) / 256;
-    k_order_hist<<<blocks, 256, 0, st>>>(w, hist, mode, bands);
-    k_order_scatter<<<1, 1024, 0, st>>>(w, hist, order, mode, bands);
+    k_order_hist<<<blocks, 256, 0, st>>>(w, hist, mode, bands, in);
+    k_order_scatter<<<1, 1024, 0, st>>>(w, hist, order, mode, bands, in);
     return cudaGetLastError();
 }
 

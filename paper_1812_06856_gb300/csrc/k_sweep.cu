@@ -249,79 +249,94 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
     }
 }
 
-// one CTA per superpixel
-// camera-frame sweeps: 6 CTAs of 256 threads (12 of 128) per SM, at most 40 registers;
-// world-frame sweeps (more FP64 per label) 4, at most 64
+// camera-frame sweeps: 6 CTAs of 256 threads (12 of 128) per SM, at most 40
+// registers; world-frame sweeps (more FP64 per label) 4, at most 64
+
+// one CTA per superpixel of order_sweep[base .. base + count)
 template <int FMT, bool WORLD, int THREADS, bool AFF>
-__global__ void __launch_bounds__(THREADS, (WORLD ? 1024 : 1536) / THREADS) k_sweep(Workspace w, Consts c, float4 *planes, int *label_out,
-                                                   float *cost_out)
+__global__ void __launch_bounds__(THREADS, (WORLD ? 1024 : 1536) / THREADS) k_sweep(Workspace w, Consts c, int base,
+                                                                                     float4 *planes, int *label_out,
+                                                                                     float *cost_out)
 {
     __shared__ SweepShared<THREADS, WORLD> sh;
-    sweep_sp<FMT, WORLD, THREADS, AFF>(w, c, blockIdx.x, sh, planes, label_out, cost_out);
+    sweep_sp<FMT, WORLD, THREADS, AFF>(w, c, __ldg(w.order_sweep + base + blockIdx.x), sh, planes, label_out,
+                                       cost_out);
 }
 
-// persistent CTAs: superpixels taken from the size-ordered queue, largest class first
+// persistent CTAs: superpixels of order_sweep[base .. base + count) taken in
+// order (size classes, largest first), queue counter queue[qidx]
 template <int FMT, bool WORLD, int THREADS, bool AFF>
-__global__ void __launch_bounds__(THREADS, (WORLD ? 1024 : 1536) / THREADS) k_sweep_persistent(Workspace w, Consts c, float4 *planes, int *label_out,
-                                                              float *cost_out)
+__global__ void __launch_bounds__(THREADS, (WORLD ? 1024 : 1536) / THREADS) k_sweep_persistent(
+    Workspace w, Consts c, int base, int count, int qidx, float4 *planes, int *label_out, float *cost_out)
 {
     __shared__ SweepShared<THREADS, WORLD> sh;
     for (;;) {
-        if (threadIdx.x == 0) sh.item = atomicAdd(&w.queue[0], 1);
+        if (threadIdx.x == 0) sh.item = atomicAdd(&w.queue[qidx], 1);
         __syncthreads();
         const int item = sh.item;
         __syncthreads();
-        if (item >= w.S_total) break;
-        sweep_sp<FMT, WORLD, THREADS, AFF>(w, c, __ldg(w.order_sweep + item), sh, planes, label_out, cost_out);
+        if (item >= count) break;
+        sweep_sp<FMT, WORLD, THREADS, AFF>(w, c, __ldg(w.order_sweep + base + item), sh, planes, label_out, cost_out);
         __syncthreads();
     }
 }
 
 template <int FMT, bool WORLD, int THREADS, bool AFF>
-static cudaError_t launch_sweep_a(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
-                                  float *cost, cudaStream_t st)
+static cudaError_t launch_sweep_a(const Workspace &w, const Consts &c, const LaunchCfg &lc, int base, int count,
+                                  int qidx, float4 *planes, int *label, float *cost, cudaStream_t st)
 {
+    if (count <= 0) return cudaSuccess;
     if (lc.sweep_persistent) {
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, k_sweep_persistent<FMT, WORLD, THREADS, AFF>, THREADS, 0);
         if (e != cudaSuccess) return e;
-        const int grid = max(1, min(w.S_total, per_sm * lc.num_sms));
-        k_sweep_persistent<FMT, WORLD, THREADS, AFF><<<grid, THREADS, 0, st>>>(w, c, planes, label, cost);
+        const int grid = max(1, min(count, per_sm * lc.num_sms));
+        k_sweep_persistent<FMT, WORLD, THREADS, AFF><<<grid, THREADS, 0, st>>>(w, c, base, count, qidx, planes,
+                                                                               label, cost);
     } else {
-        k_sweep<FMT, WORLD, THREADS, AFF><<<w.S_total, THREADS, 0, st>>>(w, c, planes, label, cost);
+        k_sweep<FMT, WORLD, THREADS, AFF><<<count, THREADS, 0, st>>>(w, c, base, planes, label, cost);
     }
     return cudaGetLastError();
 }
 
 template <int FMT, bool WORLD, int THREADS>
-static cudaError_t launch_sweep_t(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
-                                  float *cost, cudaStream_t st)
+static cudaError_t launch_sweep_t(const Workspace &w, const Consts &c, const LaunchCfg &lc, int base, int count,
+                                  int qidx, float4 *planes, int *label, float *cost, cudaStream_t st)
 {
-    if (!WORLD && c.affine) return launch_sweep_a<FMT, false, THREADS, true>(w, c, lc, planes, label, cost, st);
-    return launch_sweep_a<FMT, WORLD, THREADS, false>(w, c, lc, planes, label, cost, st);
+    if (!WORLD && c.affine)
+        return launch_sweep_a<FMT, false, THREADS, true>(w, c, lc, base, count, qidx, planes, label, cost, st);
+    return launch_sweep_a<FMT, WORLD, THREADS, false>(w, c, lc, base, count, qidx, planes, label, cost, st);
 }
 
 template <int FMT>
-static cudaError_t launch_sweep_f(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
-                                  float *cost, cudaStream_t st)
+static cudaError_t launch_sweep_f(const Workspace &w, const Consts &c, const LaunchCfg &lc, int threads, int base,
+                                  int count, int qidx, float4 *planes, int *label, float *cost, cudaStream_t st)
 {
-    if (c.sweep_frame) {
-        return lc.sweep_threads == 128 ? launch_sweep_t<FMT, true, 128>(w, c, lc, planes, label, cost, st)
-                                       : launch_sweep_t<FMT, true, 256>(w, c, lc, planes, label, cost, st);
+    if (c.sweep_frame)   // world-frame sweeps: 128 or 256 threads
+        return threads <= 128 ? launch_sweep_t<FMT, true, 128>(w, c, lc, base, count, qidx, planes, label, cost, st)
+                              : launch_sweep_t<FMT, true, 256>(w, c, lc, base, count, qidx, planes, label, cost, st);
+    switch (threads) {
+    case 64: return launch_sweep_t<FMT, false, 64>(w, c, lc, base, count, qidx, planes, label, cost, st);
+    case 128: return launch_sweep_t<FMT, false, 128>(w, c, lc, base, count, qidx, planes, label, cost, st);
+    case 160: return launch_sweep_t<FMT, false, 160>(w, c, lc, base, count, qidx, planes, label, cost, st);
+    case 192: return launch_sweep_t<FMT, false, 192>(w, c, lc, base, count, qidx, planes, label, cost, st);
+    case 224: return launch_sweep_t<FMT, false, 224>(w, c, lc, base, count, qidx, planes, label, cost, st);
+    default: return launch_sweep_t<FMT, false, 256>(w, c, lc, base, count, qidx, planes, label, cost, st);
     }
-    return lc.sweep_threads == 128 ? launch_sweep_t<FMT, false, 128>(w, c, lc, planes, label, cost, st)
-                                   : launch_sweep_t<FMT, false, 256>(w, c, lc, planes, label, cost, st);
 }
 
-cudaError_t launch_sweep(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
-                         float *cost, cudaStream_t st)
+cudaError_t launch_sweep(const Workspace &w, const Consts &c, const LaunchCfg &lc, int threads, int base, int count,
+                         int qidx, float4 *planes, int *label, float *cost, cudaStream_t st)
 {
     switch (c.fmt) {
-    case LFD_RGBA8: return launch_sweep_f<LFD_RGBA8>(w, c, lc, planes, label, cost, st);
-    case LFD_RGBA_F16: return launch_sweep_f<LFD_RGBA_F16>(w, c, lc, planes, label, cost, st);
-    case LFD_RGBA_BF16: return launch_sweep_f<LFD_RGBA_BF16>(w, c, lc, planes, label, cost, st);
-    case LFD_RGBA_F32: return launch_sweep_f<LFD_RGBA_F32>(w, c, lc, planes, label, cost, st);
+    case LFD_RGBA8: return launch_sweep_f<LFD_RGBA8>(w, c, lc, threads, base, count, qidx, planes, label, cost, st);
+    case LFD_RGBA_F16:
+        return launch_sweep_f<LFD_RGBA_F16>(w, c, lc, threads, base, count, qidx, planes, label, cost, st);
+    case LFD_RGBA_BF16:
+        return launch_sweep_f<LFD_RGBA_BF16>(w, c, lc, threads, base, count, qidx, planes, label, cost, st);
+    case LFD_RGBA_F32:
+        return launch_sweep_f<LFD_RGBA_F32>(w, c, lc, threads, base, count, qidx, planes, label, cost, st);
     default: return cudaErrorInvalidValue;
     }
 }

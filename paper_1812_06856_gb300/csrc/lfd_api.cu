@@ -241,6 +241,8 @@ struct lfd_ctx {
     int h_bdepth_cap = 0;
     cudaEvent_t ev_bdepth = nullptr;
     uint64_t tuned_sig = 0;
+    // sweep launches: superpixels of label-count class c at order_sweep[cls_base[c] ..+ cls_count[c])
+    int cls_base[LCLASSES] = {}, cls_count[LCLASSES] = {};
 };
 
 namespace {
@@ -365,6 +367,7 @@ void view_params(ViewDev &d, const lfd_params &p, int fmt, int lf)
     d.xy_hi = (float)(1.0 + p.xy_eps);
     d.perturb_k = p.perturb_samples;
     d.perturb_scale = p.perturb_scale;
+    d.lclass = label_class(p.num_labels);
 }
 
 lfd_status ensure_pinned(lfd_ctx *ctx, size_t bytes)
@@ -464,7 +467,7 @@ size_t workspace_need(const Layout &L, int fmt)
     add(4 * S); add(4 * (S + 1)); add(4 * S); add(4 * P);
     add(8 * S); add(16 * S); add(16 * S); add(32 * S); add(16 * S); add(16 * S);
     add(sizeof(DevCounters));
-    add(4 * S); add(4 * S); add(4 * ORDER_KEYS_HOST); add(16); add(sizeof(float *) * V);
+    add(4 * S); add(4 * S); add(4 * ORDER_KEYS_HOST); add(64); add(sizeof(float *) * V);
     add(16 * S); add(16 * S); add(4 * S); add(8 * S); add(8 * S);
     for (int v = 0; v < V; v++) add((size_t)qb * (L.W[v] + 1) * (L.H[v] + 1));
     for (int v = 0; v < V; v++) add((size_t)16 * L.W[v] * L.H[v]);
@@ -525,7 +528,7 @@ lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
     ctx->d_order = (int *)a.take(4 * S);
     ctx->d_order_sweep = (int *)a.take(4 * S);
     ctx->d_hist = (int *)a.take(4 * ORDER_KEYS_HOST);
-    ctx->d_queue = (int *)a.take(16);
+    ctx->d_queue = (int *)a.take(64);
     ctx->d_depth_ptrs = (float **)a.take(sizeof(float *) * V);
     ctx->d_planesA = (float4 *)a.take(16 * S);
     ctx->d_planesB = (float4 *)a.take(16 * S);
@@ -699,6 +702,44 @@ lfd_status plan_input(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, const lfd_
             if (pd.P[6] != 0.0 || pd.P[7] != 0.0 || pd.q[2] != 0.0) affine = 0;
         }
     ctx->c.affine = affine;
+    // the sweep order is partitioned by label-count class, classes ascending
+    for (int k = 0; k < LCLASSES; k++) ctx->cls_count[k] = 0;
+    for (const LfInfo &l : ctx->lfs) {
+        int S_l = 0;
+        for (int v = 0; v < l.V; v++) S_l += L.S[l.first_view + v];
+        ctx->cls_count[label_class(l.p.num_labels)] += S_l;
+    }
+    for (int k = 0, b = 0; k < LCLASSES; k++) {
+        ctx->cls_base[k] = b;
+        b += ctx->cls_count[k];
+    }
+    return LFD_OK;
+}
+
+// Work orders of the persistent launches (k_superpixels.cu): the sweep's by
+// size class and row band, then partitioned by label-count class when the
+// bound light fields have several (d_order serves as the scratch of that
+// pass before it receives the propagation's order).
+lfd_status build_orders(lfd_ctx *ctx, cudaStream_t st)
+{
+    const int bands = ctx->lc.order_bands;
+    int classes = 0;
+    for (int k = 0; k < LCLASSES; k++) classes += ctx->cls_count[k] > 0;
+    if (classes > 1) {
+        LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
+            return launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, 1, bands, nullptr, st);
+        }, 2));
+        LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
+            return launch_sp_order(ctx->w, ctx->d_order_sweep, ctx->d_hist, 2, bands, ctx->d_order, st);
+        }, 2));
+    } else {
+        LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
+            return launch_sp_order(ctx->w, ctx->d_order_sweep, ctx->d_hist, 1, bands, nullptr, st);
+        }, 2));
+    }
+    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
+        return launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, 0, bands, nullptr, st);
+    }, 2));
     return LFD_OK;
 }
 
@@ -733,12 +774,8 @@ lfd_status enqueue_input(lfd_ctx *ctx, cudaStream_t st, bool record_event)
     LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] { return launch_quads(ctx->w, V, max_quads, ctx->fmt, st); }));
     // work orders: propagation by descending slot class, the sweep by descending
     // power-of-two size class, index order inside a class
-    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
-        return launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, 0, ctx->lc.order_bands, st);
-    }, 2));
-    LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
-        return launch_sp_order(ctx->w, ctx->d_order_sweep, ctx->d_hist, 1, ctx->lc.order_bands, st);
-    }, 2));
+    const lfd_status so = build_orders(ctx, st);
+    if (so != LFD_OK) return so;
     return LFD_OK;
 }
 
@@ -815,12 +852,19 @@ lfd_status rasterize_state(lfd_ctx *ctx, const float4 *planes, float *const *dep
     return LFD_OK;
 }
 
+// One sweep launch per label-count class present, CTAs as wide as the class
+// (at most lc.sweep_threads).
 lfd_status run_sweep(lfd_ctx *ctx, float *cost, cudaStream_t st)
 {
-    if (ctx->lc.sweep_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 16, st));
-    LFD_CUDA(traced(ctx, LFD_STAGE_SWEEP, st, [&] {
-        return launch_sweep(ctx->w, ctx->c, ctx->lc, ctx->d_planesA, ctx->d_label, cost, st);
-    }));
+    if (ctx->lc.sweep_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 64, st));
+    for (int k = 0; k < LCLASSES; k++) {
+        if (!ctx->cls_count[k]) continue;
+        const int threads = std::min(LCLASS_THREADS[k], ctx->lc.sweep_threads);
+        LFD_CUDA(traced(ctx, LFD_STAGE_SWEEP, st, [&] {
+            return launch_sweep(ctx->w, ctx->c, ctx->lc, threads, ctx->cls_base[k], ctx->cls_count[k], 4 + k,
+                                ctx->d_planesA, ctx->d_label, cost, st);
+        }));
+    }
     return LFD_OK;
 }
 
@@ -831,7 +875,7 @@ lfd_status iterate_flat(lfd_ctx *ctx, int iter, const float4 *in, float4 *out, i
 {
     lfd_status s;
     if ((s = rasterize_state(ctx, in, nullptr, st)) != LFD_OK) return s;
-    if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 16, st));
+    if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 64, st));
     Consts c = ctx->c;
     c.batch_iters = frame ? 1 : 0;
     LFD_CUDA(traced(ctx, LFD_STAGE_PROPAGATE, st, [&] {
@@ -906,9 +950,13 @@ lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
         ms = t[1];
         return LFD_OK;
     };
-    auto order = [&](int mode, int bands) -> lfd_status {
-        LFD_CUDA(launch_sp_order(ctx->w, mode == 0 ? ctx->d_order : ctx->d_order_sweep, ctx->d_hist, mode, bands, st));
-        return LFD_OK;
+    auto order = [&](int mode, int bands) -> lfd_status {    // mode 0: propagation, 1: sweep orders
+        const int keep = ctx->lc.order_bands;
+        ctx->lc.order_bands = bands;
+        lfd_status so = build_orders(ctx, st);
+        ctx->lc.order_bands = keep;
+        (void)mode;
+        return so;
     };
     lfd_status s;
     LaunchCfg best = ctx->lc;
@@ -948,7 +996,7 @@ lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
                     ctx->lc.prop_batch = cb[ci];
                     float ms = 0;
                     auto fn = [&]() -> lfd_status {
-                        if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 16, st));
+                        if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 64, st));
                         LFD_CUDA(launch_propagate(ctx->w, ctx->c, ctx->lc, 1, ctx->d_planesA, ctx->d_planesB, nullptr,
                                                   nullptr, st));
                         return LFD_OK;

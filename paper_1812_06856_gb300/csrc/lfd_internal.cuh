@@ -57,7 +57,8 @@ struct ViewDev {
     float xy_lo, xy_hi;      // X/Y split: inverse domain X iff zeta >= D xy_lo; depth domain X iff z <= D xy_hi
     float col_gain;          // sqrt(k_col): scale of the colours in the rasterised maps
     float dep_gain;          // sqrt(k_sig): scale of their depth values
-    int perturb_k, pad5;     // perturbation samples of the refinement (flagged variant; 0 = off)
+    int perturb_k;           // perturbation samples of the refinement (flagged variant; 0 = off)
+    int lclass;              // label-count class of its light field (sweep CTA width, LCLASS_THREADS)
     double perturb_scale;    // their relative radius at I = 1
 };
 
@@ -112,7 +113,7 @@ struct Workspace {
     DevCounters *ctr;
     const int *order;        // [S_total] work order: descending pixel-slot class, index order inside
     const int *order_sweep;  // [S_total] sweep work order: descending power-of-two size class, index order inside
-    int *queue;              // [4] work-queue counters of persistent launches
+    int *queue;              // [16] work-queue counters of persistent launches
     int S_total;
     long long px_total;
 };
@@ -264,11 +265,27 @@ cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStr
 constexpr int ORDER_CLASSES = 17;
 constexpr int ORDER_BANDS = 16;
 constexpr int ORDER_KEYS = ORDER_CLASSES * ORDER_BANDS;
-// bands: 1 .. ORDER_BANDS row bands inside a size class
-cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, int bands,
+// Label-count classes of the sweep: a light field of L labels is swept by
+// CTAs of LCLASS_THREADS[c] threads, the smallest width >= L (256 beyond:
+// several passes), so that few threads idle when L is not a multiple of 256.
+constexpr int LCLASSES = 6;
+constexpr int LCLASS_THREADS[LCLASSES] = {64, 128, 160, 192, 224, 256};
+inline int label_class(int L)
+{
+    for (int c = 0; c < LCLASSES; c++)
+        if (L <= LCLASS_THREADS[c]) return c;
+    return LCLASSES - 1;
+}
+// mode 0: propagation order (pixel-slot class, band); 1: sweep order
+// (power-of-two size class, band); 2: stable partition of `in` by the
+// label-count class of each superpixel's light field.  bands: 1 ..
+// ORDER_BANDS row bands inside a size class.  in: NULL = index order.
+cudaError_t launch_sp_order(const Workspace &w, int *order, int *hist, int mode, int bands, const int *in,
                             cudaStream_t st);  // hist: ORDER_KEYS ints
-cudaError_t launch_sweep(const Workspace &w, const Consts &c, const LaunchCfg &lc, float4 *planes, int *label,
-                         float *cost, cudaStream_t st);
+// sweep of the superpixels order_sweep[base .. base + count) with CTAs of
+// `threads` threads (one of LCLASS_THREADS), queue counter queue[qidx]
+cudaError_t launch_sweep(const Workspace &w, const Consts &c, const LaunchCfg &lc, int threads, int base, int count,
+                         int qidx, float4 *planes, int *label, float *cost, cudaStream_t st);
 cudaError_t launch_plane_prep(const Workspace &w, const Consts &c, const float4 *planes, double4_32a *g, float4 *rc,
                               cudaStream_t st);
 cudaError_t launch_rasterize(const Workspace &w, const Consts &c, float *const *depth, cudaStream_t st);
