@@ -50,8 +50,9 @@ L2_FLUSH_BYTES = 256 << 20
 # Gathered bytes (the level that bounds a gather-heavy kernel): the sweep's
 # bilinear sample reads a 2x2 block of source texels (4 texels of 4 B for
 # RGBA8, 8 B for FP16/BF16, 16 B for FP32; neighbouring samples share them),
-# the energy sample one rasterised texel {superpixel label, depth} of 8 B (the
-# superpixel colours are a small table that stays in L1).
+# the energy sample what one rasterised pixel carries, the superpixel it
+# belongs to and its depth: 8 B (this implementation gathers a 16-B texel
+# {superpixel colour, depth} instead, which saves the dependent colour lookup).
 # FP32 operations: sweep ~40 (homography column 3, reciprocal 1, floor and
 # fraction 4, bilinear 3 x 3 FMA + weight 1, SSD 3 + 3, truncation and
 # accumulation 2 ...), energy ~17 (projection 6 + 2, reciprocal 1, Eq. 9 colour
@@ -260,7 +261,7 @@ def build_inputs(cfg: int, device: str, scale: float = 1.0):
 
 # superpixel fraction of each configuration that the oracle scores for the
 # CPU baseline (about 10 s of host work) and per reference step
-CPU_SAMPLE = {1: 1.0, 2: 0.25, 3: 0.03}
+CPU_SAMPLE = {1: 1.0, 2: 0.25, 3: 0.03, 4: 0.05}
 REF_SAMPLE = {1: 0.2, 2: 0.004, 3: 0.004}
 
 
@@ -663,7 +664,8 @@ def run_ours_batch(args):
         orc.build()
         o = orc.Oracle(*synth.oracle_inputs(lf0), m0.params, threads=cores)
         rng = np.random.default_rng(1234)
-        n = max(cores, int(round(args.cpu_sample * o.S_total)))
+        frac = args.cpu_sample if args.cpu_sample is not None else CPU_SAMPLE[4]
+        n = max(cores, int(round(frac * o.S_total)))
         sample_items = np.sort(rng.choice(o.S_total, size=n, replace=False)).astype(np.int32)
         h, dt = oracle_sample_step(o, m0.params, sample_items)
         line["cpu_baseline"] = {"value": h / dt, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -291,7 +291,9 @@ cudaError_t launch_sp_minw(const Workspace &w, const Consts &c, float4 *col, cud
 // ---------------------------------------------------------------------------
 //   RGBA8: bilinear coefficients as exact halves               24 B / pixel
 //          (16-B records for all entries, then 8-B records)
-//   F16/BF16: 2 x uint4 {t00, t10}, {t01, t11} (8 B texels)  32 B / pixel
+//   F16/BF16: red/green of t00, t10, t01, t11 as four half   24 B / pixel
+//          pairs (16-B records for all entries), then blue of
+//          (t00, t10), (t01, t11) as two pairs (8-B records)
 //   F32: 3 x float4 RGB of t00, t10, t01, t11                48 B / pixel
 //   (W + 1) x (H + 1) entries per view, see k_quads
 
@@ -338,11 +340,13 @@ __global__ void __launch_bounds__(256) k_quads(Workspace w, int fmt)
                                            pack_h2(by[0], by[1]));
         ((uint2 *)((uint4 *)vd.quad + npx))[p] = make_uint2(pack_h2(by[2], bxy[0]), pack_h2(bxy[1], bxy[2]));
     } else if (fmt == LFD_RGBA_F16 || fmt == LFD_RGBA_BF16) {
+        // a texel is {red|green, blue|alpha} as two 16-bit pairs
         const uint2 *a = (const uint2 *)r0, *b = (const uint2 *)r1;
         const uint2 t00 = a[x], t10 = a[x1], t01 = b[x], t11 = b[x1];
-        uint4 *q = (uint4 *)vd.quad + 2 * (long long)p;
-        q[0] = make_uint4(t00.x, t00.y, t10.x, t10.y);
-        q[1] = make_uint4(t01.x, t01.y, t11.x, t11.y);
+        const long long npx = (long long)Wp * (vd.H + 1);
+        ((uint4 *)vd.quad)[p] = make_uint4(t00.x, t10.x, t01.x, t11.x);
+        ((uint2 *)((uint4 *)vd.quad + npx))[p] =
+            make_uint2((t00.y & 0xffffu) | (t10.y << 16), (t01.y & 0xffffu) | (t11.y << 16));
     } else {
         const float4 *a = (const float4 *)r0, *b = (const float4 *)r1;
         const float4 t00 = a[x], t10 = a[x1], t01 = b[x], t11 = b[x1];

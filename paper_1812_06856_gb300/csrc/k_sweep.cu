@@ -27,6 +27,20 @@ namespace lfd {
 
 constexpr int SWEEP_CHUNK = 128;
 
+// Pair forms of the homography of a (view, neighbour view) pair, the kernels'
+// template argument PF:
+//   PF_GENERAL  any pair;
+//   PF_AFFINE   P row 3 = (0, 0, P22) and q_z = 0 (parallel optical axes at
+//               equal depth): the sample's homogeneous coordinate is the same
+//               for every pixel of a label;
+//   PF_SHIFT    affine with P's upper 2 x 2 block = P22 I as well (rectified
+//               parallel cameras with equal intrinsics, e.g. a planar array):
+//               a fronto-parallel plane moves every pixel by the same vector
+//               (X0, Y0), so the integer part and the bilinear fractions are
+//               per label and view, and a sample is an integer offset, a
+//               window test on it and the gather.
+constexpr int PF_GENERAL = 0, PF_AFFINE = 1, PF_SHIFT = 2;
+
 struct SweepPair {
     float a00, a01, a10, a11, a20, a21;   // FP32 columns 0,1 of P (camera frame: not label dependent)
     int Wi, Hi;
@@ -52,7 +66,7 @@ struct SweepShared {
 };
 
 // the whole sweep of superpixel gs by one CTA (threads = labels)
-template <int FMT, bool WORLD, int THREADS, bool AFF>
+template <int FMT, bool WORLD, int THREADS, int PF>
 __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, int gs, SweepShared<THREADS, WORLD> &sh,
                                          float4 *planes, int *label_out, float *cost_out)
 {
@@ -145,8 +159,15 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
                     const int j = t / cn, i = t - j * cn;
                     const SweepPair &sp = sh.pair[j];
                     const float2 d = sh.d[i];
-                    sh.xyw[j][i] = make_float4(fmaf(sp.a00, d.x, sp.a01 * d.y), fmaf(sp.a10, d.x, sp.a11 * d.y),
-                                               fmaf(sp.a20, d.x, sp.a21 * d.y), 0.f);
+                    if (PF == PF_SHIFT) {
+                        // the pixel offset and its offset in view j's sampling texture
+                        const int du = (int)d.x, dv = (int)d.y;
+                        sh.xyw[j][i] = make_float4(__int_as_float(du), __int_as_float(dv),
+                                                   __int_as_float(dv * (sp.Wi + 1) + du), 0.f);
+                    } else {
+                        sh.xyw[j][i] = make_float4(fmaf(sp.a00, d.x, sp.a01 * d.y), fmaf(sp.a10, d.x, sp.a11 * d.y),
+                                                   fmaf(sp.a20, d.x, sp.a21 * d.y), 0.f);
+                    }
                 }
             }
             __syncthreads();
@@ -177,7 +198,35 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
                         if (rc.w == 0.f) t = T;
                         cost += t;
                     }
-                } else if (AFF) {
+                } else if (PF == PF_SHIFT) {
+                    // translation pair: pixel offset (du, dv) samples at (du + X0, dv + Y0);
+                    // with ix = du + floor(X0) and fx = X0 - floor(X0) the texture-area
+                    // test -1/2 <= ix + fx < Wi - 1/2 is lo <= ix <= lo + Wi - 1, lo = -1
+                    // when fx >= 1/2 and 0 otherwise (the same for y)
+                    const float4 *xyw = sh.xyw[WORLD ? 0 : j];
+                    const float rw = rcp_approx(cw);
+                    const float X0 = cx * rw, Y0 = cy * rw;
+                    if (cw > 0.f && fabsf(X0) < 1e9f && fabsf(Y0) < 1e9f) {
+                        const float xf = floorf(X0), yf = floorf(Y0);
+                        const float fx = X0 - xf, fy = Y0 - yf;
+                        const int ixk = (int)xf, iyk = (int)yf;
+                        const int ox = ixk + (fx >= 0.5f ? 1 : 0), oy = iyk + (fy >= 0.5f ? 1 : 0);
+                        const unsigned spx = (unsigned)(Wi - 1), spy = (unsigned)(Hi - 1);
+                        const long long koff = quad_index(ixk, iyk, Wi), npx = quad_entries(Wi, Hi);
+#pragma unroll 4
+                        for (int i = 0; i < cn; i++) {
+                            const float4 q = xyw[i];
+                            const float4 rc = sh.ref[i];
+                            const bool in = (unsigned)(__float_as_int(q.x) + ox) <= spx &&
+                                            (unsigned)(__float_as_int(q.y) + oy) <= spy;
+                            cost += in ? tssd_quad<FMT>(tex, koff + __float_as_int(q.z), npx, fx, fy,
+                                                        make_float3(rc.x, rc.y, rc.z), T)
+                                       : T;
+                        }
+                    } else {
+                        for (int i = 0; i < cn; i++) cost += T;
+                    }
+                } else if (PF == PF_AFFINE) {
                     // affine pair: the homogeneous coordinate is cw for every pixel
                     // (P row 3 = (0, 0, P22), q_z = 0), one reciprocal per label and view;
                     // the same arithmetic as the general loop, value for value
@@ -253,19 +302,19 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
 // registers; world-frame sweeps (more FP64 per label) 4, at most 64
 
 // one CTA per superpixel of order_sweep[base .. base + count)
-template <int FMT, bool WORLD, int THREADS, bool AFF>
+template <int FMT, bool WORLD, int THREADS, int PF>
 __global__ void __launch_bounds__(THREADS, (WORLD ? 1024 : 1536) / THREADS) k_sweep(Workspace w, Consts c, int base,
                                                                                      float4 *planes, int *label_out,
                                                                                      float *cost_out)
 {
     __shared__ SweepShared<THREADS, WORLD> sh;
-    sweep_sp<FMT, WORLD, THREADS, AFF>(w, c, __ldg(w.order_sweep + base + blockIdx.x), sh, planes, label_out,
+    sweep_sp<FMT, WORLD, THREADS, PF>(w, c, __ldg(w.order_sweep + base + blockIdx.x), sh, planes, label_out,
                                        cost_out);
 }
 
 // persistent CTAs: superpixels of order_sweep[base .. base + count) taken in
 // order (size classes, largest first), queue counter queue[qidx]
-template <int FMT, bool WORLD, int THREADS, bool AFF>
+template <int FMT, bool WORLD, int THREADS, int PF>
 __global__ void __launch_bounds__(THREADS, (WORLD ? 1024 : 1536) / THREADS) k_sweep_persistent(
     Workspace w, Consts c, int base, int count, int qidx, float4 *planes, int *label_out, float *cost_out)
 {
@@ -276,12 +325,12 @@ __global__ void __launch_bounds__(THREADS, (WORLD ? 1024 : 1536) / THREADS) k_sw
         const int item = sh.item;
         __syncthreads();
         if (item >= count) break;
-        sweep_sp<FMT, WORLD, THREADS, AFF>(w, c, __ldg(w.order_sweep + base + item), sh, planes, label_out, cost_out);
+        sweep_sp<FMT, WORLD, THREADS, PF>(w, c, __ldg(w.order_sweep + base + item), sh, planes, label_out, cost_out);
         __syncthreads();
     }
 }
 
-template <int FMT, bool WORLD, int THREADS, bool AFF>
+template <int FMT, bool WORLD, int THREADS, int PF>
 static cudaError_t launch_sweep_a(const Workspace &w, const Consts &c, const LaunchCfg &lc, int base, int count,
                                   int qidx, float4 *planes, int *label, float *cost, cudaStream_t st)
 {
@@ -289,13 +338,13 @@ static cudaError_t launch_sweep_a(const Workspace &w, const Consts &c, const Lau
     if (lc.sweep_persistent) {
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_sweep_persistent<FMT, WORLD, THREADS, AFF>, THREADS, 0);
+            &per_sm, k_sweep_persistent<FMT, WORLD, THREADS, PF>, THREADS, 0);
         if (e != cudaSuccess) return e;
         const int grid = max(1, min(count, per_sm * lc.num_sms));
-        k_sweep_persistent<FMT, WORLD, THREADS, AFF><<<grid, THREADS, 0, st>>>(w, c, base, count, qidx, planes,
+        k_sweep_persistent<FMT, WORLD, THREADS, PF><<<grid, THREADS, 0, st>>>(w, c, base, count, qidx, planes,
                                                                                label, cost);
     } else {
-        k_sweep<FMT, WORLD, THREADS, AFF><<<count, THREADS, 0, st>>>(w, c, base, planes, label, cost);
+        k_sweep<FMT, WORLD, THREADS, PF><<<count, THREADS, 0, st>>>(w, c, base, planes, label, cost);
     }
     return cudaGetLastError();
 }
@@ -304,9 +353,11 @@ template <int FMT, bool WORLD, int THREADS>
 static cudaError_t launch_sweep_t(const Workspace &w, const Consts &c, const LaunchCfg &lc, int base, int count,
                                   int qidx, float4 *planes, int *label, float *cost, cudaStream_t st)
 {
+    if (!WORLD && c.affine && c.shift)
+        return launch_sweep_a<FMT, false, THREADS, PF_SHIFT>(w, c, lc, base, count, qidx, planes, label, cost, st);
     if (!WORLD && c.affine)
-        return launch_sweep_a<FMT, false, THREADS, true>(w, c, lc, base, count, qidx, planes, label, cost, st);
-    return launch_sweep_a<FMT, WORLD, THREADS, false>(w, c, lc, base, count, qidx, planes, label, cost, st);
+        return launch_sweep_a<FMT, false, THREADS, PF_AFFINE>(w, c, lc, base, count, qidx, planes, label, cost, st);
+    return launch_sweep_a<FMT, WORLD, THREADS, PF_GENERAL>(w, c, lc, base, count, qidx, planes, label, cost, st);
 }
 
 template <int FMT>

@@ -92,7 +92,7 @@ int quad_bytes(int fmt)
 {
     switch (fmt) {
     case LFD_RGBA8: return 24;
-    case LFD_RGBA_F16: case LFD_RGBA_BF16: return 32;
+    case LFD_RGBA_F16: case LFD_RGBA_BF16: return 24;
     case LFD_RGBA_F32: return 48;
     default: return 0;
     }
@@ -694,14 +694,22 @@ lfd_status plan_input(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, const lfd_
     // affine pairs: P row 3 = (0, 0, P22) and q_z = 0, so A(g) = P + q g^T keeps
     // row 3 = (0, 0, P22) for every plane g (cameras with parallel optical axes
     // and equal z in the reference frame, e.g. planar arrays)
-    int affine = 1;
+    // translation pairs: affine with P's upper 2 x 2 block = P22 I to within
+    // 1e-12 relative (rectified cameras with equal intrinsics): a pixel offset
+    // du < 2^16 then moves by less than 1e-7 px against the exact homography
+    int affine = 1, shift = 1;
     for (int v = 0; v < V; v++)
         for (int k = 0; k < LFD_MAXN; k++) {
             if (ctx->nbr[(size_t)v * LFD_MAXN + k] < 0) continue;
             const PairDev &pd = hp[v * LFD_MAXN + k];
             if (pd.P[6] != 0.0 || pd.P[7] != 0.0 || pd.q[2] != 0.0) affine = 0;
+            const double e = 1e-12 * std::fabs(pd.P[8]);
+            if (!(pd.P[8] > 0.0) || std::fabs(pd.P[0] - pd.P[8]) > e || std::fabs(pd.P[4] - pd.P[8]) > e ||
+                std::fabs(pd.P[1]) > e || std::fabs(pd.P[3]) > e)
+                shift = 0;
         }
     ctx->c.affine = affine;
+    ctx->c.shift = affine && shift;
     // the sweep order is partitioned by label-count class, classes ascending
     for (int k = 0; k < LCLASSES; k++) ctx->cls_count[k] = 0;
     for (const LfInfo &l : ctx->lfs) {

@@ -94,6 +94,10 @@ struct Consts {
     int affine;              // 1: every pair's homography has third row (0, 0, c) for every plane
                              //    (parallel cameras, common principal depth axis): the sample's depth
                              //    term is constant per (hypothesis, view) and the kernels skip it
+    int shift;               // 1: affine, and every pair's P has upper 2 x 2 block P22 I (rectified
+                             //    cameras with equal intrinsics): a fronto-parallel sweep plane
+                             //    translates the image, the sweep samples at integer offsets plus
+                             //    per-label fractions
 };
 
 struct Workspace {

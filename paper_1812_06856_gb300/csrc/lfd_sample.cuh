@@ -47,19 +47,22 @@ __device__ __forceinline__ float2 bf2f(unsigned u)
 
 // The 2x2 texels of a float quad: rg[k] = (red, green) of texel k (k = 0
 // (x,y), 1 (x+1,y), 2 (x,y+1), 3 (x+1,y+1)) as a pair for the packed
-// arithmetic, b[k] its blue.
+// arithmetic, b[k] its blue.  FP16/BF16 entries: a 16-B record of the four
+// red/green pairs and an 8-B record of the blues (b0, b1), (b2, b3), the
+// second array starting after npx 16-B records.
 template <>
 struct Quad<LFD_RGBA_F16> {
     float2 rg[4];
     float b[4];
-    __device__ __forceinline__ void load(const void *tex, long long idx)
+    __device__ __forceinline__ void load(const void *tex, long long idx, long long npx)
     {
-        const uint4 *q = (const uint4 *)tex + 2 * idx;
-        const uint4 a = __ldg(q), c = __ldg(q + 1);
-        rg[0] = h2f(a.x); b[0] = h2f(a.y).x;
-        rg[1] = h2f(a.z); b[1] = h2f(a.w).x;
-        rg[2] = h2f(c.x); b[2] = h2f(c.y).x;
-        rg[3] = h2f(c.z); b[3] = h2f(c.w).x;
+        const uint4 a = __ldg((const uint4 *)tex + idx);
+        const uint2 e = __ldg((const uint2 *)((const uint4 *)tex + npx) + idx);
+        rg[0] = h2f(a.x); rg[1] = h2f(a.y); rg[2] = h2f(a.z); rg[3] = h2f(a.w);
+        float2 t = h2f(e.x);
+        b[0] = t.x; b[1] = t.y;
+        t = h2f(e.y);
+        b[2] = t.x; b[3] = t.y;
     }
 };
 
@@ -67,14 +70,15 @@ template <>
 struct Quad<LFD_RGBA_BF16> {
     float2 rg[4];
     float b[4];
-    __device__ __forceinline__ void load(const void *tex, long long idx)
+    __device__ __forceinline__ void load(const void *tex, long long idx, long long npx)
     {
-        const uint4 *q = (const uint4 *)tex + 2 * idx;
-        const uint4 a = __ldg(q), c = __ldg(q + 1);
-        rg[0] = bf2f(a.x); b[0] = bf2f(a.y).x;
-        rg[1] = bf2f(a.z); b[1] = bf2f(a.w).x;
-        rg[2] = bf2f(c.x); b[2] = bf2f(c.y).x;
-        rg[3] = bf2f(c.z); b[3] = bf2f(c.w).x;
+        const uint4 a = __ldg((const uint4 *)tex + idx);
+        const uint2 e = __ldg((const uint2 *)((const uint4 *)tex + npx) + idx);
+        rg[0] = bf2f(a.x); rg[1] = bf2f(a.y); rg[2] = bf2f(a.z); rg[3] = bf2f(a.w);
+        float2 t = bf2f(e.x);
+        b[0] = t.x; b[1] = t.y;
+        t = bf2f(e.y);
+        b[2] = t.x; b[3] = t.y;
     }
 };
 
@@ -82,7 +86,7 @@ template <>
 struct Quad<LFD_RGBA_F32> {
     float2 rg[4];
     float b[4];
-    __device__ __forceinline__ void load(const void *tex, long long idx)
+    __device__ __forceinline__ void load(const void *tex, long long idx, long long)
     {
         const float4 *q = (const float4 *)tex + 3 * idx;
         const float4 a = __ldg(q), c = __ldg(q + 1), d = __ldg(q + 2);
@@ -113,8 +117,41 @@ __device__ __forceinline__ float3 texel_colour(const void *tex, int x, int y, in
         return make_float3(t0.x, t0.y, t1.x);
     } else {
         Quad<FMT> q;
-        q.load(tex, idx);
+        q.load(tex, idx, npx);
         return make_float3(q.rg[0].x, q.rg[0].y, q.b[0]);
+    }
+}
+
+// Truncated SSD of Eq. 1 between the reference colour `ref` and the bilinear
+// sample of the quad at entry idx of view i's texture (the 2 x 2 texels from
+// pixel (x0, y0), idx = quad_index(x0, y0, Wi)) at fractions (fx, fy) in
+// [0, 1); npx = quad_entries(Wi, Hi).
+template <int FMT>
+__device__ __forceinline__ float tssd_quad(const void *tex, long long idx, long long npx, float fx, float fy,
+                                           float3 ref, float T)
+{
+    if constexpr (FMT == LFD_RGBA8) {
+        Coef8 q;
+        q.load(tex, idx, npx);
+        const float fxy = fx * fy;
+        const float dr = ref.x - fmaf(fxy, q.bxy[0], fmaf(fy, q.by[0], fmaf(fx, q.bx[0], q.a[0])));
+        const float dg = ref.y - fmaf(fxy, q.bxy[1], fmaf(fy, q.by[1], fmaf(fx, q.bx[1], q.a[1])));
+        const float db = ref.z - fmaf(fxy, q.bxy[2], fmaf(fy, q.by[2], fmaf(fx, q.bx[2], q.a[2])));
+        return fminf(fmaf(dr, dr, fmaf(dg, dg, db * db)), T);
+    } else {
+        // red and green as packed pairs, blue alone: the same lerps as scalar
+        // code, half the issue slots for two of the channels
+        Quad<FMT> q;
+        q.load(tex, idx, npx);
+        const float2 FX = dup2(fx);
+        const float2 top = ffma2(FX, fsub2(q.rg[1], q.rg[0]), q.rg[0]);
+        const float2 bot = ffma2(FX, fsub2(q.rg[3], q.rg[2]), q.rg[2]);
+        const float2 rg = ffma2(dup2(fy), fsub2(bot, top), top);
+        const float b0 = fmaf(fx, q.b[1] - q.b[0], q.b[0]), b1 = fmaf(fx, q.b[3] - q.b[2], q.b[2]);
+        const float2 d = fsub2(make_float2(ref.x, ref.y), rg);
+        const float2 d2 = fmul2(d, d);
+        const float db = ref.z - fmaf(fy, b1 - b0, b0);
+        return fminf(fmaf(db, db, d2.x + d2.y), T);
     }
 }
 
@@ -131,31 +168,7 @@ __device__ __forceinline__ float tssd_at(const void *tex, int Wi, int Hi, float 
     const bool ok = (x >= -0.5f) && (x < (float)Wi - 0.5f) && (y >= -0.5f) && (y < (float)Hi - 0.5f);
     if (!ok) return T;
     const float xf = floorf(x), yf = floorf(y);          // -1 .. W-1, -1 .. H-1
-    const float fx = x - xf, fy = y - yf;
-    const long long idx = quad_index((int)xf, (int)yf, Wi);
-    if constexpr (FMT == LFD_RGBA8) {
-        Coef8 q;
-        q.load(tex, idx, quad_entries(Wi, Hi));
-        const float fxy = fx * fy;
-        const float dr = ref.x - fmaf(fxy, q.bxy[0], fmaf(fy, q.by[0], fmaf(fx, q.bx[0], q.a[0])));
-        const float dg = ref.y - fmaf(fxy, q.bxy[1], fmaf(fy, q.by[1], fmaf(fx, q.bx[1], q.a[1])));
-        const float db = ref.z - fmaf(fxy, q.bxy[2], fmaf(fy, q.by[2], fmaf(fx, q.bx[2], q.a[2])));
-        return fminf(fmaf(dr, dr, fmaf(dg, dg, db * db)), T);
-    } else {
-        // red and green as packed pairs, blue alone: the same lerps as scalar
-        // code, half the issue slots for two of the channels
-        Quad<FMT> q;
-        q.load(tex, idx);
-        const float2 FX = dup2(fx);
-        const float2 top = ffma2(FX, fsub2(q.rg[1], q.rg[0]), q.rg[0]);
-        const float2 bot = ffma2(FX, fsub2(q.rg[3], q.rg[2]), q.rg[2]);
-        const float2 rg = ffma2(dup2(fy), fsub2(bot, top), top);
-        const float b0 = fmaf(fx, q.b[1] - q.b[0], q.b[0]), b1 = fmaf(fx, q.b[3] - q.b[2], q.b[2]);
-        const float2 d = fsub2(make_float2(ref.x, ref.y), rg);
-        const float2 d2 = fmul2(d, d);
-        const float db = ref.z - fmaf(fy, b1 - b0, b0);
-        return fminf(fmaf(db, db, d2.x + d2.y), T);
-    }
+    return tssd_quad<FMT>(tex, quad_index((int)xf, (int)yf, Wi), quad_entries(Wi, Hi), x - xf, y - yf, ref, T);
 }
 
 template <int FMT>
