@@ -293,7 +293,7 @@ cudaError_t launch_sp_minw(const Workspace &w, const Consts &c, float4 *col, cud
 //          (16-B records for all entries, then 8-B records)
 //   F16/BF16: red/green of t00, t10, t01, t11 as four half   24 B / pixel
 //          pairs (16-B records for all entries), then blue of
-//          (t00, t10), (t01, t11) as two pairs (8-B records)
+//          (t00, t01), (t10, t11) as two pairs (8-B records)
 //   F32: 3 x float4 RGB of t00, t10, t01, t11                48 B / pixel
 //   (W + 1) x (H + 1) entries per view, see k_quads
 
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(256) k_quads(Workspace w, int fmt)
         const long long npx = (long long)Wp * (vd.H + 1);
         ((uint4 *)vd.quad)[p] = make_uint4(t00.x, t10.x, t01.x, t11.x);
         ((uint2 *)((uint4 *)vd.quad + npx))[p] =
-            make_uint2((t00.y & 0xffffu) | (t10.y << 16), (t01.y & 0xffffu) | (t11.y << 16));
+            make_uint2((t00.y & 0xffffu) | (t01.y << 16), (t10.y & 0xffffu) | (t11.y << 16));
     } else {
         const float4 *a = (const float4 *)r0, *b = (const float4 *)r1;
         const float4 t00 = a[x], t10 = a[x1], t01 = b[x], t11 = b[x1];

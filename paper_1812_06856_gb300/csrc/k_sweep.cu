@@ -219,9 +219,10 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
                             const float4 rc = sh.ref[i];
                             const bool in = (unsigned)(__float_as_int(q.x) + ox) <= spx &&
                                             (unsigned)(__float_as_int(q.y) + oy) <= spy;
-                            cost += in ? tssd_quad<FMT>(tex, koff + __float_as_int(q.z), npx, fx, fy,
-                                                        make_float3(rc.x, rc.y, rc.z), T)
-                                       : T;
+                            // branch-free: a sample off the texture area reads entry 0
+                            const long long e = in ? koff + __float_as_int(q.z) : 0;
+                            const float t = tssd_quad<FMT>(tex, e, npx, fx, fy, make_float3(rc.x, rc.y, rc.z), T);
+                            cost += in ? t : T;
                         }
                     } else {
                         for (int i = 0; i < cn; i++) cost += T;

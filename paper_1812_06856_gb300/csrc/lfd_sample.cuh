@@ -45,55 +45,55 @@ __device__ __forceinline__ float2 bf2f(unsigned u)
     return __bfloat1622float2(h);
 }
 
-// The 2x2 texels of a float quad: rg[k] = (red, green) of texel k (k = 0
-// (x,y), 1 (x+1,y), 2 (x,y+1), 3 (x+1,y+1)) as a pair for the packed
-// arithmetic, b[k] its blue.  FP16/BF16 entries: a 16-B record of the four
-// red/green pairs and an 8-B record of the blues (b0, b1), (b2, b3), the
-// second array starting after npx 16-B records.
+// The 2x2 texels of a float quad (k = 0 (x,y), 1 (x+1,y), 2 (x,y+1),
+// 3 (x+1,y+1)): rg[k] = (red, green) of texel k, and the blues as the
+// column pairs b02 = (b0, b2), b13 = (b1, b3), each a pair for the packed
+// arithmetic (the x lerp of both rows of blue is one packed lerp).
+// FP16/BF16 entries: a 16-B record of the four red/green pairs and an 8-B
+// record of the two blue pairs, the second array starting after npx 16-B
+// records.
 template <>
 struct Quad<LFD_RGBA_F16> {
     float2 rg[4];
-    float b[4];
+    float2 b02, b13;
     __device__ __forceinline__ void load(const void *tex, long long idx, long long npx)
     {
         const uint4 a = __ldg((const uint4 *)tex + idx);
         const uint2 e = __ldg((const uint2 *)((const uint4 *)tex + npx) + idx);
         rg[0] = h2f(a.x); rg[1] = h2f(a.y); rg[2] = h2f(a.z); rg[3] = h2f(a.w);
-        float2 t = h2f(e.x);
-        b[0] = t.x; b[1] = t.y;
-        t = h2f(e.y);
-        b[2] = t.x; b[3] = t.y;
+        b02 = h2f(e.x);
+        b13 = h2f(e.y);
     }
 };
 
 template <>
 struct Quad<LFD_RGBA_BF16> {
     float2 rg[4];
-    float b[4];
+    float2 b02, b13;
     __device__ __forceinline__ void load(const void *tex, long long idx, long long npx)
     {
         const uint4 a = __ldg((const uint4 *)tex + idx);
         const uint2 e = __ldg((const uint2 *)((const uint4 *)tex + npx) + idx);
         rg[0] = bf2f(a.x); rg[1] = bf2f(a.y); rg[2] = bf2f(a.z); rg[3] = bf2f(a.w);
-        float2 t = bf2f(e.x);
-        b[0] = t.x; b[1] = t.y;
-        t = bf2f(e.y);
-        b[2] = t.x; b[3] = t.y;
+        b02 = bf2f(e.x);
+        b13 = bf2f(e.y);
     }
 };
 
 template <>
 struct Quad<LFD_RGBA_F32> {
     float2 rg[4];
-    float b[4];
+    float2 b02, b13;
     __device__ __forceinline__ void load(const void *tex, long long idx, long long)
     {
         const float4 *q = (const float4 *)tex + 3 * idx;
         const float4 a = __ldg(q), c = __ldg(q + 1), d = __ldg(q + 2);
-        rg[0] = make_float2(a.x, a.y); b[0] = a.z;
-        rg[1] = make_float2(a.w, c.x); b[1] = c.y;
-        rg[2] = make_float2(c.z, c.w); b[2] = d.x;
-        rg[3] = make_float2(d.y, d.z); b[3] = d.w;
+        rg[0] = make_float2(a.x, a.y);
+        rg[1] = make_float2(a.w, c.x);
+        rg[2] = make_float2(c.z, c.w);
+        rg[3] = make_float2(d.y, d.z);
+        b02 = make_float2(a.z, d.x);
+        b13 = make_float2(c.y, d.w);
     }
 };
 
@@ -118,7 +118,7 @@ __device__ __forceinline__ float3 texel_colour(const void *tex, int x, int y, in
     } else {
         Quad<FMT> q;
         q.load(tex, idx, npx);
-        return make_float3(q.rg[0].x, q.rg[0].y, q.b[0]);
+        return make_float3(q.rg[0].x, q.rg[0].y, q.b02.x);
     }
 }
 
@@ -139,18 +139,18 @@ __device__ __forceinline__ float tssd_quad(const void *tex, long long idx, long 
         const float db = ref.z - fmaf(fxy, q.bxy[2], fmaf(fy, q.by[2], fmaf(fx, q.bx[2], q.a[2])));
         return fminf(fmaf(dr, dr, fmaf(dg, dg, db * db)), T);
     } else {
-        // red and green as packed pairs, blue alone: the same lerps as scalar
-        // code, half the issue slots for two of the channels
+        // red/green of a row and blue of both rows as packed pairs: the same
+        // lerps as scalar code in fewer issue slots
         Quad<FMT> q;
         q.load(tex, idx, npx);
         const float2 FX = dup2(fx);
         const float2 top = ffma2(FX, fsub2(q.rg[1], q.rg[0]), q.rg[0]);
         const float2 bot = ffma2(FX, fsub2(q.rg[3], q.rg[2]), q.rg[2]);
         const float2 rg = ffma2(dup2(fy), fsub2(bot, top), top);
-        const float b0 = fmaf(fx, q.b[1] - q.b[0], q.b[0]), b1 = fmaf(fx, q.b[3] - q.b[2], q.b[2]);
+        const float2 bb = ffma2(FX, fsub2(q.b13, q.b02), q.b02);       // (top, bottom) blue
         const float2 d = fsub2(make_float2(ref.x, ref.y), rg);
         const float2 d2 = fmul2(d, d);
-        const float db = ref.z - fmaf(fy, b1 - b0, b0);
+        const float db = ref.z - fmaf(fy, bb.y - bb.x, bb.x);
         return fminf(fmaf(db, db, d2.x + d2.y), T);
     }
 }
