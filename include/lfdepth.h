@@ -361,6 +361,30 @@ lfd_status lfd_workspace_required(int32_t n, const lfd_lightfield *lfs, uint64_t
  * prop_blocks, prop_persistent, prop_batch, order_bands. */
 lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out);
 
+/* Homography specialisations of the plane-induced homography A(g) = P + q g^T
+ * (Section III-B; the pair's P = K_i R_rel K_v^-1, q = K_i t_rel).  When
+ * binding an input the library classifies all its (view, neighbour view)
+ * pairs together:
+ *   0 general:     any cameras;
+ *   1 affine:      every pair has P row 3 = (0, 0, P22) and q_z = 0 (parallel
+ *                  optical axes, camera centres at equal depth): the
+ *                  homogeneous coordinate of a sample is the same for all
+ *                  pixels of a hypothesis, one reciprocal per (hypothesis,
+ *                  view); results are the general form's, value for value;
+ *   2 translation: affine and P's upper 2 x 2 block = P22 I to 1e-12
+ *                  (rectified cameras with equal intrinsics): a
+ *                  fronto-parallel sweep plane moves every pixel by one
+ *                  vector; the sweep's costs differ from the general form's by
+ *                  FP32 rounding of the sample position only (the
+ *                  propagation uses form 1).
+ * lfd_set_pair_forms(ctx, max_form): the largest form the context may use
+ * for inputs bound after the call (0, 1 or 2; default 2; LFD_ERR_INVALID_ARG
+ * otherwise); drops a captured CUDA graph.
+ * lfd_pair_form(ctx, &form): the form of the bound input (LFD_ERR_STATE
+ * before one is bound). */
+lfd_status lfd_set_pair_forms(lfd_ctx *ctx, int32_t max_form);
+lfd_status lfd_pair_form(const lfd_ctx *ctx, int32_t *form);
+
 /* ---- serving ---------------------------------------------------------- */
 
 /* A frame server: several rigs (camera arrays, each a stream of light-field

@@ -184,6 +184,7 @@ struct lfd_ctx {
     std::vector<int> nbr;          // [V_total * 8] global view indices
     int fmt = 0;
     LaunchCfg lc{256, 1, 8, 1, 0, 32, ORDER_BANDS};
+    int max_pair_form = 2;         // largest homography specialisation allowed (lfd_set_pair_forms)
     // workspace
     Arena ws;
     Workspace w{};
@@ -708,8 +709,8 @@ lfd_status plan_input(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, const lfd_
                 std::fabs(pd.P[1]) > e || std::fabs(pd.P[3]) > e)
                 shift = 0;
         }
-    ctx->c.affine = affine;
-    ctx->c.shift = affine && shift;
+    ctx->c.affine = affine && ctx->max_pair_form >= 1;
+    ctx->c.shift = affine && shift && ctx->max_pair_form >= 2;
     // the sweep order is partitioned by label-count class, classes ascending
     for (int k = 0; k < LCLASSES; k++) ctx->cls_count[k] = 0;
     for (const LfInfo &l : ctx->lfs) {
@@ -1747,6 +1748,21 @@ lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out)
     out[3] = ctx->lc.prop_persistent;
     out[4] = ctx->lc.prop_batch;
     out[5] = ctx->lc.order_bands;
+    return LFD_OK;
+}
+lfd_status lfd_set_pair_forms(lfd_ctx *ctx, int32_t max_form)
+{
+    if (!ctx) return LFD_ERR_INVALID_ARG;
+    if (max_form < 0 || max_form > 2) return fail(ctx, LFD_ERR_INVALID_ARG, "max_form must be 0, 1 or 2");
+    ctx->max_pair_form = max_form;
+    drop_graph(ctx);
+    return LFD_OK;
+}
+lfd_status lfd_pair_form(const lfd_ctx *ctx, int32_t *form)
+{
+    if (!ctx || !form) return LFD_ERR_INVALID_ARG;
+    if (!ctx->bound) return LFD_ERR_STATE;
+    *form = ctx->c.shift ? 2 : (ctx->c.affine ? 1 : 0);
     return LFD_OK;
 }
 lfd_status lfd_synchronize(lfd_ctx *ctx, void *stream)

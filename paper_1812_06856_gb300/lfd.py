@@ -126,6 +126,8 @@ def load(build_if_missing: bool = True):
     lib.lfd_estimate_batch_warm.argtypes = [vp, i32, P(LightFieldC), P(Params), P(vp), P(vp), P(vp),
                                             P(BatchOptions), vp]
     lib.lfd_launch_config.argtypes = [vp, P(i32)]
+    lib.lfd_set_pair_forms.argtypes = [vp, i32]
+    lib.lfd_pair_form.argtypes = [vp, P(i32)]
     lib.lfd_workspace_required.argtypes = [i32, P(LightFieldC), P(C.c_uint64)]
     lib.lfd_fuse.argtypes = [vp, P(vp), P(vp), C.c_double, vp]
     lib.lfd_slic.argtypes = [vp, i32, P(vp), vp, i32, vp, vp, vp, vp, C.c_double, i32, P(vp), P(vp), P(vp), vp]
@@ -145,7 +147,7 @@ def load(build_if_missing: bool = True):
     for name in ("lfd_create", "lfd_destroy", "lfd_set_input", "lfd_num_superpixels", "lfd_plane_sweep",
                  "lfd_rasterize", "lfd_iterate", "lfd_estimate", "lfd_estimate_host", "lfd_synchronize",
                  "lfd_counters", "lfd_score", "lfd_get_superpixels", "lfd_neighbor_views", "lfd_profile_enable",
-                 "lfd_profile_read", "lfd_estimate_batch", "lfd_estimate_batch_warm", "lfd_launch_config", "lfd_workspace_required", "lfd_fuse", "lfd_slic",
+                 "lfd_profile_read", "lfd_estimate_batch", "lfd_estimate_batch_warm", "lfd_launch_config", "lfd_set_pair_forms", "lfd_pair_form", "lfd_workspace_required", "lfd_fuse", "lfd_slic",
                  "lfd_server_create", "lfd_server_destroy", "lfd_server_configure", "lfd_server_submit",
                  "lfd_server_poll", "lfd_server_export_state", "lfd_server_import_state", "lfd_server_set_max_batch",
                  "lfd_server_stats"):
@@ -535,6 +537,17 @@ class Context:
         self._check(self.lib.lfd_launch_config(self.h, out), "lfd_launch_config")
         return dict(sweep_threads=out[0], sweep_persistent=out[1], prop_blocks=out[2], prop_persistent=out[3],
                     prop_batch=out[4], order_bands=out[5])
+
+    def set_pair_forms(self, max_form: int):
+        """Largest homography specialisation (0 general, 1 affine, 2 translation)
+        used for inputs bound after the call."""
+        self._check(self.lib.lfd_set_pair_forms(self.h, int(max_form)), "lfd_set_pair_forms")
+
+    def pair_form(self) -> int:
+        """Specialisation of the bound input: 0 general, 1 affine, 2 translation."""
+        out = C.c_int32()
+        self._check(self.lib.lfd_pair_form(self.h, C.byref(out)), "lfd_pair_form")
+        return int(out.value)
 
     def synchronize(self, stream=None):
         self._check(self.lib.lfd_synchronize(self.h, _stream(stream)), "lfd_synchronize")
