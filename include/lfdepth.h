@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define LFD_VERSION 1
+#define LFD_VERSION 2
 #define LFD_MAX_NEIGHBOR_VIEWS 8   /* |N(v)| of Eq. 2 / Eq. 8 is at most this */
 #define LFD_MAX_VIEWS 256
 #define LFD_MAX_LABELS 4096
@@ -291,14 +291,14 @@ lfd_status lfd_fuse(lfd_ctx *ctx, const float *const *depth_in, float *const *de
 
 /* Launch options of lfd_estimate_batch (lfd_batch_options_default fills
  * autotune 0, graph 0, sweep_threads 256, sweep_persistent 1, prop_blocks 8,
- * prop_persistent 1, prop_batch 32, order_bands 16). */
+ * prop_persistent 1, prop_batch 32, order_bands 16, prop_coop 0). */
 typedef struct {
     int32_t autotune;          /* 1: the first call with a new argument signature times, on its
                                   own input, the sweep (128/256 threads x grid/persistent x
                                   1/16 row bands in the work order) and the propagation (7/8
-                                  CTAs per SM x grid/persistent x 16/32 candidates per batch x
-                                  1/16 row bands) and keeps the fastest of each; the shape
-                                  fields are then ignored */
+                                  CTAs per SM x grid/persistent warps/cooperative CTAs x 16/32
+                                  candidates per batch x 1/16 row bands) and keeps the fastest
+                                  of each; the shape fields are then ignored */
     int32_t graph;             /* 1: the frame's device work is captured as a CUDA graph on the
                                   first call; a later call whose signature (every pointer, size,
                                   camera, parameter and option) is identical replays it, reading
@@ -313,6 +313,12 @@ typedef struct {
                                   neighbour views (their footprints share L1 across the pass) */
     int32_t order_bands;       /* 1 or 16 (0 = 16): row bands of the work orders inside a size class
                                   (16: the superpixels in flight cover the same rows of every view) */
+    int32_t prop_coop;         /* 1 (with prop_persistent): the 4 warps of a propagation CTA update
+                                  one superpixel together, its candidates split between them, so
+                                  they gather from one footprint per neighbour view (L1 reuse);
+                                  0: one superpixel per warp.  Same results either way; on the
+                                  16 x 1080p and 8 x 1024x768 frames 0 is faster (the kernel is
+                                  issue-bound and the split costs instructions and barriers). */
 } lfd_batch_options;
 
 void lfd_batch_options_default(lfd_batch_options *o);
@@ -357,8 +363,8 @@ lfd_status lfd_estimate_batch_warm(lfd_ctx *ctx, int32_t n, const lfd_lightfield
  * cameras, grid sizes and pixel format. */
 lfd_status lfd_workspace_required(int32_t n, const lfd_lightfield *lfs, uint64_t *bytes);
 
-/* The launch shape in use: out[0..5] = sweep_threads, sweep_persistent,
- * prop_blocks, prop_persistent, prop_batch, order_bands. */
+/* The launch shape in use: out[0..6] = sweep_threads, sweep_persistent,
+ * prop_blocks, prop_persistent, prop_batch, order_bands, prop_coop. */
 lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out);
 
 /* Homography specialisations of the plane-induced homography A(g) = P + q g^T

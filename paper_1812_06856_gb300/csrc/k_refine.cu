@@ -253,6 +253,31 @@ struct alignas(16) CandShared {
 __shared__ SpShared g_sh[PROP_WARPS];
 __shared__ CandShared g_cs[PROP_WARPS];
 
+// Cooperative propagation (k_propagate_coop): the CTA's 4 warps refine one
+// superpixel together, so its record is per CTA; each warp keeps its own
+// candidate batch.  The winners of the warps and the candidate index of
+// every batch slot meet in CoopShared.
+struct CoopShared {
+    int item, ok;
+    int cnt[PROP_WARPS];                 // valid candidates found by each warp in a round
+    int mi[PROP_WARPS][32];              // candidate index m of batch slot (warp, slot)
+    float E[PROP_WARPS];                 // each warp's best energy, its m (or t) and plane
+    int m[PROP_WARPS];
+    double ig[PROP_WARPS];
+    float nx[PROP_WARPS], ny[PROP_WARPS], nz[PROP_WARPS];
+    unsigned nh[PROP_WARPS];             // hypotheses scored per warp
+};
+__shared__ SpShared g_shc[1];
+__shared__ CoopShared g_co;
+
+// the superpixel record of this warp: its own, or the CTA's in the cooperative form
+template <bool COOP>
+__device__ __forceinline__ SpShared &sp_shared()
+{
+    if constexpr (COOP) return g_shc[0];
+    else return g_sh[threadIdx.x >> 5];
+}
+
 struct Acc {
     unsigned cnt, nx, ny;
     float sw, sg;
@@ -399,11 +424,11 @@ __device__ __forceinline__ void energy_sample(const ViewK &K, bool act, float du
 // terms of lfd_score to `rec`.  Lane c keeps candidate c's running sum in a
 // register (the reduced terms are identical in every lane), so the loop has
 // no divergent store.
-template <int DOMAIN, int SL, bool MASK_ALL = false, bool REC = false, bool AFF = false>
+template <int DOMAIN, int SL, bool MASK_ALL = false, bool REC = false, bool AFF = false, bool COOP = false>
 __device__ __noinline__ void view_terms(const Workspace &w, unsigned mask, float *rec)
 {
     const int lane = threadIdx.x & 31;
-    const SpShared &sh = g_sh[threadIdx.x >> 5];
+    const SpShared &sh = sp_shared<COOP>();
     CandShared &cs = g_cs[threadIdx.x >> 5];
     const WarpSP S = sh.S;
     float ec = cs.ec[lane];
@@ -639,14 +664,14 @@ __device__ bool setup_sp(const Workspace &w, const float4 *planes_in, int gs, in
     return true;
 }
 
-// Refinement candidate t = lane (Fig. 3b): the normal of the triangle of the
-// own centroid at depth dnew and ring neighbours t, t+1 at their depths,
-// facing the camera; false for a missing vertex, a degenerate or a grazing
-// triangle.  The plane goes to the warp's CandShared slot t.
-template <int DOMAIN>
-__device__ __noinline__ bool triangle_candidate(const ViewDev &vd, double dnew, double ignew, int t)
+// Refinement candidate t (Fig. 3b): the normal of the triangle of the own
+// centroid at depth dnew and ring neighbours t, t+1 at their depths, facing
+// the camera; false for a missing vertex, a degenerate or a grazing
+// triangle.  The plane goes to slot `slot` of the warp's CandShared.
+template <int DOMAIN, bool COOP = false>
+__device__ __noinline__ bool triangle_candidate(const ViewDev &vd, double dnew, double ignew, int t, int slot)
 {
-    const SpShared &sh = g_sh[threadIdx.x >> 5];
+    const SpShared &sh = sp_shared<COOP>();
     CandShared &cs = g_cs[threadIdx.x >> 5];
     const SpNb &A = sh.nb[t];
     const SpNb &B = sh.nb[(t + 1) & 7];
@@ -661,12 +686,12 @@ __device__ __noinline__ bool triangle_candidate(const ViewDev &vd, double dnew, 
     const double inn = rsqrt64(nn2);
     nx *= inn; ny *= inn; nz *= inn;
     if (nx * P0x + ny * P0y + nz * P0z > 0.0) { nx = -nx; ny = -ny; nz = -nz; }   // face the camera
-    cs.nx[t] = (float)nx; cs.ny[t] = (float)ny; cs.nz[t] = (float)nz;
-    cs.ig[t] = dnew;
+    cs.nx[slot] = (float)nx; cs.ny[slot] = (float)ny; cs.nz[slot] = (float)nz;
+    cs.ig[slot] = dnew;
     if (!(fabs(nx * sh.rx + ny * sh.ry + nz * sh.rz) >= 0.1 * sh.rn)) return false;   // not grazing
     double tg0 = 0, tg1 = 0, tg2 = 0;
     if (!plane_to_g(vd, dnew, nx, ny, nz, sh.cx, sh.cy, tg0, tg1, tg2)) return false;
-    cand_store(cs, t, hyp_prep<DOMAIN>(sh.S, sh, tg0, tg1, ignew));   // g . (c,1) = 1 / dnew
+    cand_store(cs, slot, hyp_prep<DOMAIN>(sh.S, sh, tg0, tg1, ignew));   // g . (c,1) = 1 / dnew
     return true;
 }
 
@@ -675,11 +700,11 @@ __device__ __noinline__ bool triangle_candidate(const ViewDev &vd, double dnew, 
 // 1 + r (2u - 1) and normal moved by r (2u - 1) per component, r =
 // perturb_scale 2^(1 - I), draws from perturb_u; false when the depth leaves
 // [d_min, d_max] or the plane is grazing.
-template <int DOMAIN>
+template <int DOMAIN, bool COOP = false>
 __device__ __noinline__ bool perturb_candidate(const ViewDev &vd, double dnew, double n0, double n1, double n2, int I,
                                                int k, int slot)
 {
-    const SpShared &sh = g_sh[threadIdx.x >> 5];
+    const SpShared &sh = sp_shared<COOP>();
     CandShared &cs = g_cs[threadIdx.x >> 5];
     const double rad = ldexp(vd.perturb_scale, 1 - I);
     double u[4];
@@ -807,7 +832,7 @@ __device__ __noinline__ void propagate_sp(const Workspace &w, int iter, int gs, 
     if (Ebest > -INFINITY && dnew > 0.0) {
         bool ok = false;
         if (lane < 8) {
-            ok = triangle_candidate<DOMAIN>(vd, dnew, ignew, lane);
+            ok = triangle_candidate<DOMAIN>(vd, dnew, ignew, lane, lane);
         } else if (lane < 8 + vd.perturb_k) {           // flagged variant: random planes around (dnew, n)
             double n0, n1, n2;
             if (best_m > 0) {
@@ -894,6 +919,285 @@ __device__ __forceinline__ void propagate_one(const Workspace &w, const Consts &
     }
 }
 
+// ---------------------------------------------------------------------------
+// cooperative propagation: the CTA's 4 warps update one superpixel
+// ---------------------------------------------------------------------------
+//
+// The same candidates, energies and choice as propagate_sp, split across the
+// warps of the CTA: in rounds of up to 128 candidates every thread tests one
+// candidate m, the valid ones are numbered in m order across the CTA and
+// candidate c goes to warp c mod 4, batch slot c / 4; each warp scores its
+// batch with view_terms, and the warps' winners are merged (highest energy,
+// lowest m on ties: the first maximum in m order, as the sequential scan
+// takes it).  The refinement candidates t go to warp t mod 4 the same way.
+// Every candidate's energy is computed by one warp with the code of the
+// per-warp form, so the results are the same bit for bit.  The point is
+// locality: the warps of a CTA reproject one superpixel into the same
+// neighbour view at the same time, so an SM's resident warps gather from 8
+// footprints instead of 32 and the candidates reuse them from L1.
+template <int DOMAIN, int SL, bool AFF>
+__device__ __noinline__ void propagate_sp_coop(const Workspace &w, int iter, int gs, const float4 *planes_in,
+                                               float4 *planes_out, int *choice, float *energy)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    SpShared &sh = g_shc[0];
+    CandShared &cs = g_cs[wid];
+    CoopShared &co = g_co;
+    const WarpSP &S = sh.S;
+    const dbl4 gc = w.sp_g[gs];
+    const ViewDev &vd = w.views[S.v];
+    unsigned n_hyp = 0;
+
+    const int ii = min(iter + vd.warm_off, LFD_MAX_ITER_INDEX);
+    const int nr = w.radii_cnt[S.v * (LFD_MAX_ITER_INDEX + 1) + ii];
+    const short *rad = w.radii + ((long long)S.v * (LFD_MAX_ITER_INDEX + 1) + ii) * LFD_MAX_RADII;
+    const int M = 9 + 8 * nr;
+    float Ebest = -INFINITY;                 // this warp's best; its candidate in co.*[wid]
+    if (lane == 0) co.m[wid] = -1;
+    for (int base = 0; base < M; base += 32 * PROP_WARPS) {
+        const int m = base + threadIdx.x;
+        bool ok = false;
+        double g0 = 0.0, g1 = 0.0, igc = 0.0;
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        if (m == 0) {
+            ok = gc.w != 0.0;
+            g0 = gc.x; g1 = gc.y;
+            igc = gc.x * sh.cx + gc.y * sh.cy + gc.z;
+        } else if (m < M) {
+            int dx, dy;
+            if (m <= 8) {
+                ring_dir(m - 1, dx, dy);
+            } else {
+                const int t = m - 9;
+                const int r = rad[t >> 3];
+                ring_dir(t & 7, dx, dy);
+                dx *= r;
+                dy *= r;
+            }
+            const int x = S.gx + dx, y = S.gy + dy;
+            if (x >= 0 && y >= 0 && x < vd.GW && y < vd.GH) {
+                const int j = vd.sp_base + y * vd.GW + x;
+                if (__ldg(w.sp_cnt + j) > 0) {
+                    const dbl4 gj = w.sp_g[j];
+                    const double ig = gj.x * sh.cx + gj.y * sh.cy + gj.z;   // candidate's inverse depth at own centroid
+                    ok = gj.w != 0.0 && ig > 0.0 && ig >= vd.inv_dmax && ig <= vd.inv_dmin;
+                    const float4 pj = planes_in[j];
+                    const double cosr = fabs(pj.y * sh.rx + pj.z * sh.ry + pj.w * sh.rz);
+                    ok = ok && cosr >= 0.1 * sh.rn;                          // not grazing
+                    g0 = gj.x; g1 = gj.y; igc = ig;
+                    nx = pj.y; ny = pj.z; nz = pj.w;
+                }
+            }
+        }
+        // number the valid candidates of the round in m order across the CTA
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) co.cnt[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < PROP_WARPS; k++) {
+            const int ck = co.cnt[k];
+            before += k < wid ? ck : 0;
+            total += ck;
+        }
+        if (ok) {
+            const int cidx = before + __popc(bal & ((1u << lane) - 1u));
+            const int dw = cidx & (PROP_WARPS - 1), slot = cidx / PROP_WARPS;
+            CandShared &dst = g_cs[dw];
+            cand_store(dst, slot, hyp_prep<DOMAIN>(S, sh, g0, g1, igc));
+            dst.ig[slot] = igc;
+            dst.nx[slot] = nx; dst.ny[slot] = ny; dst.nz[slot] = nz;
+            dst.ec[slot] = 0.f;
+            co.mi[dw][slot] = m;
+        }
+        __syncthreads();
+        const int nw = total > wid ? (total - wid + PROP_WARPS - 1) / PROP_WARPS : 0;
+        unsigned mask = nw >= 32 ? 0xffffffffu : ((1u << nw) - 1u);
+        if (mask) view_terms<DOMAIN, SL, false, false, AFF, true>(w, mask, nullptr);
+        int sbest = -1;
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const float E = cand_energy(sh, cs, S.nnb, src);
+            n_hyp++;
+            if (E > Ebest) {
+                Ebest = E;
+                sbest = src;
+            }
+        }
+        if (sbest >= 0 && lane == 0) {       // the round's winner of this warp: keep its plane
+            co.E[wid] = Ebest;
+            co.m[wid] = co.mi[wid][sbest];
+            co.ig[wid] = cs.ig[sbest];
+            co.nx[wid] = cs.nx[sbest]; co.ny[wid] = cs.ny[sbest]; co.nz[wid] = cs.nz[sbest];
+        }
+        __syncthreads();                     // the batches are refilled next round
+    }
+    // merge: highest energy, lowest m on ties
+    float Eprop = -INFINITY;
+    int wm = -1;
+#pragma unroll
+    for (int k = 0; k < PROP_WARPS; k++) {
+        const float e = co.E[k];
+        if (co.m[k] >= 0 && (wm < 0 || e > Eprop || (e == Eprop && co.m[k] < co.m[wm]))) {
+            Eprop = e;
+            wm = k;
+        }
+    }
+    const int best_m = wm >= 0 ? co.m[wm] : 0;
+    const double best_ig = wm >= 0 ? co.ig[wm] : 0.0;
+    float pnx = 0.f, pny = 0.f, pnz = 0.f;
+    if (best_m > 0) { pnx = co.nx[wm]; pny = co.ny[wm]; pnz = co.nz[wm]; }
+    __syncthreads();                         // the records are reused by the refinement
+
+    // refinement step: normals of the eight ring triangles (Fig. 3b), candidate t
+    // in warp t mod 4, slot t / 4
+    int best_t = -1;
+    float Efinal = Eprop;
+    double tdep = 0.0;
+    float tnx = 0.f, tny = 0.f, tnz = 0.f;
+    const double dnew = best_m > 0 ? rcp64(best_ig) : (double)planes_in[gs].x;
+    const double ignew = best_m > 0 ? best_ig : rcp64(dnew);
+    if (Eprop > -INFINITY && dnew > 0.0) {
+        const int t = PROP_WARPS * lane + wid;
+        bool ok = false;
+        if (t < 8) {
+            ok = triangle_candidate<DOMAIN, true>(vd, dnew, ignew, t, lane);
+        } else if (t < 8 + vd.perturb_k) {   // flagged variant: random planes around (dnew, n)
+            double n0, n1, n2;
+            if (best_m > 0) {
+                n0 = pnx; n1 = pny; n2 = pnz;
+            } else {
+                const float4 cur = planes_in[gs];
+                n0 = cur.y; n1 = cur.z; n2 = cur.w;
+            }
+            ok = perturb_candidate<DOMAIN, true>(vd, dnew, n0, n1, n2, ii, t - 8, lane);
+        }
+        cs.ec[lane] = 0.f;
+        unsigned mask = __ballot_sync(0xffffffffu, ok);
+        __syncwarp();
+        if (mask) view_terms<DOMAIN, SL, false, false, AFF, true>(w, mask, nullptr);
+        float Et = -INFINITY;
+        int st = -1;
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const float E = cand_energy(sh, cs, S.nnb, src);
+            n_hyp++;
+            if (E > Et) {
+                Et = E;
+                st = src;
+            }
+        }
+        if (lane == 0) {
+            co.E[wid] = Et;
+            co.m[wid] = st >= 0 ? PROP_WARPS * st + wid : -1;
+            co.ig[wid] = st >= 0 ? cs.ig[st] : 0.0;
+            co.nx[wid] = st >= 0 ? cs.nx[st] : 0.f;
+            co.ny[wid] = st >= 0 ? cs.ny[st] : 0.f;
+            co.nz[wid] = st >= 0 ? cs.nz[st] : 0.f;
+        }
+        __syncthreads();
+        // the refinement winner must beat the propagation's energy; lowest t on ties
+        int wt = -1;
+        float Emax = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < PROP_WARPS; k++) {
+            const float e = co.E[k];
+            if (co.m[k] >= 0 && (wt < 0 || e > Emax || (e == Emax && co.m[k] < co.m[wt]))) {
+                Emax = e;
+                wt = k;
+            }
+        }
+        if (wt >= 0 && Emax > Eprop) {
+            best_t = co.m[wt];
+            Efinal = Emax;
+            tdep = co.ig[wt];
+            tnx = co.nx[wt]; tny = co.ny[wt]; tnz = co.nz[wt];
+        }
+    }
+    if (lane == 0) co.nh[wid] = n_hyp;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned nh = 0;
+        for (int k = 0; k < PROP_WARPS; k++) nh += co.nh[k];
+        float4 out = planes_in[gs];
+        if (best_t >= 0)
+            out = make_float4((float)tdep, tnx, tny, tnz);
+        else if (best_m > 0)
+            out = make_float4((float)dnew, pnx, pny, pnz);
+        planes_out[gs] = out;
+        if (choice) { choice[2 * gs] = best_m; choice[2 * gs + 1] = best_t; }
+        if (energy) { energy[2 * gs] = Eprop; energy[2 * gs + 1] = Efinal; }
+        atomicAdd(&w.ctr->hyp, (unsigned long long)nh);
+        atomicAdd(&w.ctr->samples, (unsigned long long)nh * S.n * S.nnb);
+    }
+}
+
+// set-up (by warp 0) and slot-count dispatch of one superpixel for the CTA
+template <int DOMAIN, bool AFF>
+__device__ __forceinline__ void propagate_one_coop(const Workspace &w, const Consts &c, int iter, int gs,
+                                                   const float4 *planes_in, float4 *planes_out, int *choice,
+                                                   float *energy)
+{
+    const int lane = threadIdx.x & 31;
+    {
+        const ViewDev &vd0 = w.views[__ldg(w.sp_view + gs)];
+        if (c.batch_iters && iter > vd0.iters) {   // this light field has finished: carry its plane through
+            if (threadIdx.x == 0) {
+                planes_out[gs] = planes_in[gs];
+                if (choice) { choice[2 * gs] = 0; choice[2 * gs + 1] = -1; }
+                if (energy) { energy[2 * gs] = -INFINITY; energy[2 * gs + 1] = -INFINITY; }
+            }
+            return;
+        }
+    }
+    SpShared &sh = g_shc[0];
+    if (threadIdx.x < 32) {
+        const dbl4 gc = w.sp_g[gs];
+        WarpSP S;
+        const bool ok = setup_sp<DOMAIN>(w, planes_in, gs, lane, S, sh, gc.w != 0.0, gc.x, gc.y, gc.z);
+        if (lane == 0) g_co.ok = ok;
+    }
+    __syncthreads();
+    if (!g_co.ok) {
+        if (threadIdx.x == 0) {
+            planes_out[gs] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (choice) { choice[2 * gs] = -1; choice[2 * gs + 1] = -1; }
+            if (energy) { energy[2 * gs] = -INFINITY; energy[2 * gs + 1] = -INFINITY; }
+        }
+        return;
+    }
+    switch (slot_class(sh.S.n)) {
+    case 1: propagate_sp_coop<DOMAIN, 1, AFF>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 2: propagate_sp_coop<DOMAIN, 2, AFF>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 3: propagate_sp_coop<DOMAIN, 3, AFF>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 4: propagate_sp_coop<DOMAIN, 4, AFF>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 5: propagate_sp_coop<DOMAIN, 5, AFF>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 6: propagate_sp_coop<DOMAIN, 6, AFF>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 7: propagate_sp_coop<DOMAIN, 7, AFF>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    case 8: propagate_sp_coop<DOMAIN, 8, AFF>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    default: propagate_sp_coop<DOMAIN, SLOTS_MAX, AFF>(w, iter, gs, planes_in, planes_out, choice, energy); break;
+    }
+}
+
+// persistent CTAs: one superpixel per CTA at a time, from the cost-ordered queue
+template <int DOMAIN, int MINB, bool AFF>
+__global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate_coop(const __grid_constant__ Workspace w, Consts c,
+                                                                          int iter, const float4 *planes_in,
+                                                                          float4 *planes_out, int *choice,
+                                                                          float *energy)
+{
+    for (;;) {
+        if (threadIdx.x == 0) g_co.item = atomicAdd(&w.queue[1], 1);
+        __syncthreads();
+        const int item = g_co.item;
+        if (item >= w.S_total) break;
+        propagate_one_coop<DOMAIN, AFF>(w, c, iter, __ldg(w.order + item), planes_in, planes_out, choice, energy);
+        __syncthreads();                     // every thread is done with this superpixel's records
+    }
+}
+
 template <int DOMAIN, int MINB, bool AFF>
 __global__ void __launch_bounds__(32 * PROP_WARPS, MINB) k_propagate(const __grid_constant__ Workspace w, Consts c, int iter,
                                                                      const float4 *planes_in, float4 *planes_out,
@@ -928,7 +1232,15 @@ static cudaError_t launch_propagate_t(const Workspace &w, const Consts &c, const
                                       const float4 *planes_in, float4 *planes_out, int *choice, float *energy,
                                       cudaStream_t st)
 {
-    if (lc.prop_persistent) {
+    if (lc.prop_persistent && lc.prop_coop) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_propagate_coop<DOMAIN, MINB, AFF>, 32 * PROP_WARPS, 0);
+        if (e != cudaSuccess) return e;
+        const int grid = max(1, min(w.S_total, per_sm * lc.num_sms));
+        k_propagate_coop<DOMAIN, MINB, AFF><<<grid, 32 * PROP_WARPS, 0, st>>>(w, c, iter, planes_in, planes_out,
+                                                                              choice, energy);
+    } else if (lc.prop_persistent) {
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, k_propagate_persistent<DOMAIN, MINB, AFF>, 32 * PROP_WARPS, 0);

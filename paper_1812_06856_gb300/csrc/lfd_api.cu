@@ -183,7 +183,7 @@ struct lfd_ctx {
     std::vector<LfInfo> lfs;
     std::vector<int> nbr;          // [V_total * 8] global view indices
     int fmt = 0;
-    LaunchCfg lc{256, 1, 8, 1, 0, 32, ORDER_BANDS};
+    LaunchCfg lc{256, 1, 8, 1, 0, 32, ORDER_BANDS, 0};
     int max_pair_form = 2;         // largest homography specialisation allowed (lfd_set_pair_forms)
     // workspace
     Arena ws;
@@ -934,8 +934,9 @@ lfd_status enqueue_frame(lfd_ctx *ctx, const float *const *warm, float *const *c
 // Launch-shape autotuner: times each sweep and propagate variant on the bound
 // input (one warm-up run, then the median of three) and keeps the fastest.
 // Axes: sweep threads 128/256 x grid/persistent x row bands 1/16 of the
-// sweep's work order; propagation CTAs per SM 7/8 x grid/persistent x
-// candidates per pass 16/32 x row bands 1/16 (iteration 1, the widest kernel).
+// sweep's work order; propagation CTAs per SM 7/8 x grid/persistent
+// warps/cooperative CTAs x candidates per pass 16/32 x row bands 1/16
+// (iteration 1, the widest kernel).
 // Results do not depend on the shape (per-superpixel work is the same).
 lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
 {
@@ -997,11 +998,12 @@ lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
     const int pb[2] = {7, 8}, cb[2] = {16, 32};
     for (int bi = 0; bi < 2; bi++) {
         if ((s = order(0, bands[bi])) != LFD_OK) return s;
-        for (int pi = 0; pi < 2; pi++)
+        for (int pi = 0; pi < 3; pi++)        // grid, persistent warps, cooperative CTAs
             for (int ki = 0; ki < 2; ki++)
                 for (int ci = 0; ci < 2; ci++) {
                     ctx->lc.prop_blocks = pb[ki];
-                    ctx->lc.prop_persistent = pi;
+                    ctx->lc.prop_persistent = pi > 0;
+                    ctx->lc.prop_coop = pi == 2;
                     ctx->lc.prop_batch = cb[ci];
                     float ms = 0;
                     auto fn = [&]() -> lfd_status {
@@ -1014,7 +1016,8 @@ lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
                     if (ms < best_ms) {
                         best_ms = ms;
                         best.prop_blocks = pb[ki];
-                        best.prop_persistent = pi;
+                        best.prop_persistent = pi > 0;
+                        best.prop_coop = pi == 2;
                         best.prop_batch = cb[ci];
                         prop_bands = bands[bi];
                     }
@@ -1089,7 +1092,7 @@ lfd_status apply_options(lfd_ctx *ctx, const lfd_batch_options &o)
         (o.prop_blocks != 0 && o.prop_blocks != 7 && o.prop_blocks != 8) || (o.sweep_persistent & ~1) ||
         (o.prop_persistent & ~1) || (o.autotune & ~1) || (o.graph & ~1) ||
         (o.prop_batch != 0 && o.prop_batch != 16 && o.prop_batch != 32) ||
-        (o.order_bands != 0 && o.order_bands != 1 && o.order_bands != ORDER_BANDS))
+        (o.order_bands != 0 && o.order_bands != 1 && o.order_bands != ORDER_BANDS) || (o.prop_coop & ~1))
         return fail(ctx, LFD_ERR_INVALID_ARG, "batch options: sweep_threads 0/128/256, prop_blocks 0/7/8, "
                                               "prop_batch 0/16/32, order_bands 0/1/16, flags 0/1");
     if (o.autotune) return LFD_OK;
@@ -1099,6 +1102,7 @@ lfd_status apply_options(lfd_ctx *ctx, const lfd_batch_options &o)
     ctx->lc.prop_persistent = o.prop_persistent;
     ctx->lc.prop_batch = o.prop_batch ? o.prop_batch : 32;
     ctx->lc.order_bands = o.order_bands ? o.order_bands : ORDER_BANDS;
+    ctx->lc.prop_coop = o.prop_coop;
     return LFD_OK;
 }
 
@@ -1176,6 +1180,7 @@ void lfd_batch_options_default(lfd_batch_options *o)
     o->prop_persistent = 1;
     o->prop_batch = 32;
     o->order_bands = ORDER_BANDS;
+    o->prop_coop = 0;
 }
 
 lfd_status lfd_create(lfd_ctx **out, int32_t device, uint64_t hbm_budget_bytes)
@@ -1748,6 +1753,7 @@ lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out)
     out[3] = ctx->lc.prop_persistent;
     out[4] = ctx->lc.prop_batch;
     out[5] = ctx->lc.order_bands;
+    out[6] = ctx->lc.prop_coop;
     return LFD_OK;
 }
 lfd_status lfd_set_pair_forms(lfd_ctx *ctx, int32_t max_form)

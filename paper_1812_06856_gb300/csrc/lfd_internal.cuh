@@ -256,6 +256,7 @@ struct LaunchCfg {
     int num_sms;
     int prop_batch;          // 16 or 32 candidate planes per pass over the neighbour views
     int order_bands;         // 1 or 16 row bands in the work orders
+    int prop_coop;           // 1: persistent CTAs whose 4 warps share one superpixel (k_propagate_coop)
 };
 
 cudaError_t launch_sp_count(const Workspace &w, int V, int max_px, int *cnt, int4 *bbox, cudaStream_t st);

@@ -61,7 +61,7 @@ class Query(C.Structure):
 class BatchOptions(C.Structure):
     _fields_ = [("autotune", C.c_int32), ("graph", C.c_int32), ("sweep_threads", C.c_int32),
                 ("sweep_persistent", C.c_int32), ("prop_blocks", C.c_int32), ("prop_persistent", C.c_int32),
-                ("prop_batch", C.c_int32), ("order_bands", C.c_int32)]
+                ("prop_batch", C.c_int32), ("order_bands", C.c_int32), ("prop_coop", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -533,10 +533,10 @@ class Context:
         return (labels, cout) if want_centres else labels
 
     def launch_config(self) -> dict:
-        out = (C.c_int32 * 6)()
+        out = (C.c_int32 * 7)()
         self._check(self.lib.lfd_launch_config(self.h, out), "lfd_launch_config")
         return dict(sweep_threads=out[0], sweep_persistent=out[1], prop_blocks=out[2], prop_persistent=out[3],
-                    prop_batch=out[4], order_bands=out[5])
+                    prop_batch=out[4], order_bands=out[5], prop_coop=out[6])
 
     def set_pair_forms(self, max_form: int):
         """Largest homography specialisation (0 general, 1 affine, 2 translation)

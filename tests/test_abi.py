@@ -48,10 +48,14 @@ def test_library_exports_every_declared_symbol(lfd):
 
 def test_struct_layouts_and_defaults(lfd):
     lib = lfd.load()
-    assert lib.lfd_version() == 1
+    assert lib.lfd_version() == 2
     p = lfd.params_struct({})
     assert (p.T, p.alpha, p.eta, p.kernel_step_sp, p.term_mask, p.jitter) == (0.04, 0.1, 0.5, 5.0, 7, 1)
     assert lib.lfd_status_string(6) == b"device-side input check failed"
+    o = lfd.BatchOptions()
+    lib.lfd_batch_options_default(ctypes.byref(o))
+    assert (o.autotune, o.graph, o.sweep_threads, o.sweep_persistent, o.prop_blocks, o.prop_persistent,
+            o.prop_batch, o.order_bands, o.prop_coop) == (0, 0, 256, 1, 8, 1, 32, 16, 0)
 
 
 @pytest.mark.parametrize("case", [(10, 2, 1), (10, 2, 2), (10, 2, 3), (10, 2, 7), (4, 8, 1), (54, 11, 1),

@@ -82,6 +82,9 @@ def test_batch_equals_separate_calls(lfd, two_rigs):
     dict(prop_batch=16),
     dict(order_bands=1),
     dict(prop_batch=16, order_bands=1, prop_persistent=0),
+    dict(prop_coop=1),
+    dict(prop_coop=1, prop_batch=16, prop_blocks=7),
+    dict(prop_coop=1, prop_batch=16, order_bands=1),
 ])
 def test_launch_shapes_give_identical_bits(lfd, two_rigs, opt):
     ctx = lfd.Context(0)
@@ -109,7 +112,7 @@ def test_autotune_picks_a_valid_shape_and_same_bits(lfd, two_rigs):
     cfg = ctx2.launch_config()
     assert cfg["sweep_threads"] in (128, 256) and cfg["prop_blocks"] in (7, 8)
     assert cfg["sweep_persistent"] in (0, 1) and cfg["prop_persistent"] in (0, 1)
-    assert cfg["prop_batch"] in (16, 32) and cfg["order_bands"] in (1, 16)
+    assert cfg["prop_batch"] in (16, 32) and cfg["order_bands"] in (1, 16) and cfg["prop_coop"] in (0, 1)
     assert torch.equal(p0, p1)
     # counters count the frame only, not the timing runs
     h, s = ctx2.counters()
