@@ -297,8 +297,9 @@ typedef struct {
                                   own input, the sweep (128/256 threads x grid/persistent x
                                   1/16 row bands in the work order) and the propagation (7/8
                                   CTAs per SM x grid/persistent warps/cooperative CTAs x 16/32
-                                  candidates per batch x 1/16 row bands) and keeps the fastest
-                                  of each; the shape fields are then ignored */
+                                  candidates per batch x 1/16 row bands, timed on the first and
+                                  the last iteration) and keeps the fastest of each; the shape
+                                  fields are then ignored */
     int32_t graph;             /* 1: the frame's device work is captured as a CUDA graph on the
                                   first call; a later call whose signature (every pointer, size,
                                   camera, parameter and option) is identical replays it, reading

@@ -936,7 +936,7 @@ lfd_status enqueue_frame(lfd_ctx *ctx, const float *const *warm, float *const *c
 // Axes: sweep threads 128/256 x grid/persistent x row bands 1/16 of the
 // sweep's work order; propagation CTAs per SM 7/8 x grid/persistent
 // warps/cooperative CTAs x candidates per pass 16/32 x row bands 1/16
-// (iteration 1, the widest kernel).
+// (timed on the first and the last iteration of the input).
 // Results do not depend on the shape (per-superpixel work is the same).
 lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
 {
@@ -996,6 +996,8 @@ lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
     if ((s = rasterize_state(ctx, ctx->d_planesA, nullptr, st)) != LFD_OK) return s;
     best_ms = 1e30f;
     const int pb[2] = {7, 8}, cb[2] = {16, 32};
+    int it_last = 1;
+    for (const LfInfo &l : ctx->lfs) it_last = std::max(it_last, l.p.iterations);
     for (int bi = 0; bi < 2; bi++) {
         if ((s = order(0, bands[bi])) != LFD_OK) return s;
         for (int pi = 0; pi < 3; pi++)        // grid, persistent warps, cooperative CTAs
@@ -1006,10 +1008,15 @@ lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
                     ctx->lc.prop_coop = pi == 2;
                     ctx->lc.prop_batch = cb[ci];
                     float ms = 0;
+                    // the first and the last iteration: the candidate count falls with the
+                    // iteration index, and a shape can win on the first and lose on the rest
                     auto fn = [&]() -> lfd_status {
-                        if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 64, st));
-                        LFD_CUDA(launch_propagate(ctx->w, ctx->c, ctx->lc, 1, ctx->d_planesA, ctx->d_planesB, nullptr,
-                                                  nullptr, st));
+                        for (int it : {1, it_last}) {
+                            if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 64, st));
+                            LFD_CUDA(launch_propagate(ctx->w, ctx->c, ctx->lc, it, ctx->d_planesA, ctx->d_planesB,
+                                                      nullptr, nullptr, st));
+                            if (it_last == 1) break;
+                        }
                         return LFD_OK;
                     };
                     if ((s = time_it(fn, ms)) != LFD_OK) return s;

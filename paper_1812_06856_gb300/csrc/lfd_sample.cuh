@@ -97,6 +97,32 @@ struct Quad<LFD_RGBA_F32> {
     }
 };
 
+// (float(lo(w)) - a.x, float(hi(w)) - a.y) for a word w of two FP16 or BF16
+// values: Blackwell's mixed-precision subtraction takes the 16-bit operand
+// as it is (the conversion is exact, one rounding as FSUB of the converted
+// values), which saves converting the second texel of each lerp.
+template <int FMT>
+__device__ __forceinline__ float2 msub2(unsigned w, float2 a)
+{
+    float2 d;
+    if constexpr (FMT == LFD_RGBA_F16)
+        asm("{\n\t.reg .f16 l, h;\n\tmov.b32 {l, h}, %2;\n\tsub.rn.f32.f16 %0, l, %3;\n\t"
+            "sub.rn.f32.f16 %1, h, %4;\n\t}"
+            : "=f"(d.x), "=f"(d.y) : "r"(w), "f"(a.x), "f"(a.y));
+    else
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tsub.rn.f32.bf16 %0, l, %3;\n\t"
+            "sub.rn.f32.bf16 %1, h, %4;\n\t}"
+            : "=f"(d.x), "=f"(d.y) : "r"(w), "f"(a.x), "f"(a.y));
+    return d;
+}
+
+template <int FMT>
+__device__ __forceinline__ float2 cvt2(unsigned w)
+{
+    if constexpr (FMT == LFD_RGBA_F16) return h2f(w);
+    else return bf2f(w);
+}
+
 // entry of pixel (x, y) in a view's sampling texture (a border of one quad
 // on the left and top, (W + 1) x (H + 1) entries; see k_quads)
 __device__ __forceinline__ long long quad_index(int x, int y, int W)
@@ -138,6 +164,22 @@ __device__ __forceinline__ float tssd_quad(const void *tex, long long idx, long 
         const float dg = ref.y - fmaf(fxy, q.bxy[1], fmaf(fy, q.by[1], fmaf(fx, q.bx[1], q.a[1])));
         const float db = ref.z - fmaf(fxy, q.bxy[2], fmaf(fy, q.by[2], fmaf(fx, q.bx[2], q.a[2])));
         return fminf(fmaf(dr, dr, fmaf(dg, dg, db * db)), T);
+    } else if constexpr (FMT == LFD_RGBA_F16 || FMT == LFD_RGBA_BF16) {
+        // the record's words as they are: the first texel of each x lerp
+        // converted, the second entering through the mixed-precision
+        // subtraction; the same values as the Quad form below
+        const uint4 a = __ldg((const uint4 *)tex + idx);
+        const uint2 e = __ldg((const uint2 *)((const uint4 *)tex + npx) + idx);
+        const float2 FX = dup2(fx);
+        const float2 r0 = cvt2<FMT>(a.x), r2 = cvt2<FMT>(a.z), b02 = cvt2<FMT>(e.x);
+        const float2 top = ffma2(FX, msub2<FMT>(a.y, r0), r0);
+        const float2 bot = ffma2(FX, msub2<FMT>(a.w, r2), r2);
+        const float2 rg = ffma2(dup2(fy), fsub2(bot, top), top);
+        const float2 bb = ffma2(FX, msub2<FMT>(e.y, b02), b02);       // (top, bottom) blue
+        const float2 d = fsub2(make_float2(ref.x, ref.y), rg);
+        const float2 d2 = fmul2(d, d);
+        const float db = ref.z - fmaf(fy, bb.y - bb.x, bb.x);
+        return fminf(fmaf(db, db, d2.x + d2.y), T);
     } else {
         // red/green of a row and blue of both rows as packed pairs: the same
         // lerps as scalar code in fewer issue slots
