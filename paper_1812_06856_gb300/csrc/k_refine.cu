@@ -375,8 +375,10 @@ __device__ __forceinline__ void sample_tail(const ViewK &K, bool act, float Nw, 
     const int idx = ok ? iy * K.Wi + ix : 0;                     // in-bounds address either way
     const float4 c = __ldg(K.map + idx);                         // {colour of the superpixel hit, depth value}
     const float tw = c.w;
-    const float dr = c.x - cr, dg = c.y - cg, db = c.z - cb;
-    const float om = ex2_approx(-fmaf(dr, dr, fmaf(dg, dg, db * db)));   // Eq. 9 summand
+    const float2 drg = fsub2(make_float2(c.x, c.y), make_float2(cr, cg));   // red, green as a packed pair
+    const float2 d2 = fmul2(drg, drg);
+    const float db = c.z - cb;
+    const float om = ex2_approx(-fmaf(db, db, d2.x + d2.y));             // Eq. 9 summand
     a.cnt += ok ? 1u : 0u;
     a.sw += ok ? om : 0.f;
     const bool has = ok && tw > 0.f;

@@ -289,11 +289,10 @@ cudaError_t launch_sp_minw(const Workspace &w, const Consts &c, float4 *col, cud
 // ---------------------------------------------------------------------------
 // 5. sampling textures: per pixel the 2x2 bilinear footprint in one record
 // ---------------------------------------------------------------------------
-//   RGBA8: bilinear coefficients as exact halves               24 B / pixel
-//          (16-B records for all entries, then 8-B records)
-//   F16/BF16: red/green of t00, t10, t01, t11 as four half   24 B / pixel
-//          pairs (16-B records for all entries), then blue of
-//          (t00, t01), (t10, t11) as two pairs (8-B records)
+//   RGBA8, F16, BF16: red/green of t00, t10, t01, t11 as     24 B / pixel
+//          four 16-bit pairs (16-B records for all entries), then
+//          blue of (t00, t01), (t10, t11) as two pairs (8-B records);
+//          RGBA8 bytes are stored as exact halves
 //   F32: 3 x float4 RGB of t00, t10, t01, t11                48 B / pixel
 //   (W + 1) x (H + 1) entries per view, see k_quads
 
@@ -324,21 +323,13 @@ __global__ void __launch_bounds__(256) k_quads(Workspace w, int fmt)
     const char *r0 = base + (long long)y * pitch;
     const char *r1 = base + (long long)y1 * pitch;
     if (fmt == LFD_RGBA8) {
+        // the byte texels as halves (0..255 exact) in the FP16 layout below
         const uchar4 *a = (const uchar4 *)r0, *b = (const uchar4 *)r1;
         const uchar4 t00 = a[x], t10 = a[x1], t01 = b[x], t11 = b[x1];
-        const int c00[3] = {t00.x, t00.y, t00.z}, c10[3] = {t10.x, t10.y, t10.z};
-        const int c01[3] = {t01.x, t01.y, t01.z}, c11[3] = {t11.x, t11.y, t11.z};
-        float av[3], bx[3], by[3], bxy[3];
-        for (int ch = 0; ch < 3; ch++) {
-            av[ch] = (float)c00[ch];
-            bx[ch] = (float)(c10[ch] - c00[ch]);
-            by[ch] = (float)(c01[ch] - c00[ch]);
-            bxy[ch] = (float)(c11[ch] - c10[ch] - c01[ch] + c00[ch]);
-        }
         const long long npx = (long long)Wp * (vd.H + 1);
-        ((uint4 *)vd.quad)[p] = make_uint4(pack_h2(av[0], av[1]), pack_h2(av[2], bx[0]), pack_h2(bx[1], bx[2]),
-                                           pack_h2(by[0], by[1]));
-        ((uint2 *)((uint4 *)vd.quad + npx))[p] = make_uint2(pack_h2(by[2], bxy[0]), pack_h2(bxy[1], bxy[2]));
+        ((uint4 *)vd.quad)[p] = make_uint4(pack_h2(t00.x, t00.y), pack_h2(t10.x, t10.y), pack_h2(t01.x, t01.y),
+                                           pack_h2(t11.x, t11.y));
+        ((uint2 *)((uint4 *)vd.quad + npx))[p] = make_uint2(pack_h2(t00.z, t01.z), pack_h2(t10.z, t11.z));
     } else if (fmt == LFD_RGBA_F16 || fmt == LFD_RGBA_BF16) {
         // a texel is {red|green, blue|alpha} as two 16-bit pairs
         const uint2 *a = (const uint2 *)r0, *b = (const uint2 *)r1;

@@ -9,29 +9,11 @@ namespace lfd {
 template <int FMT>
 struct Quad;
 
-// RGBA8 views are sampled from a coefficient-form texture: per pixel and
-// channel c(x+fx, y+fy) = a + fx bx + fy by + fx fy bxy with a = c00,
-// bx = c10 - c00, by = c01 - c00, bxy = c11 - c10 - c01 + c00.  All four are
-// integers of at most 11 bits, hence exact as IEEE halves: 12 halves = 24 B
-// per pixel, stored as a 16-B record (a.rgb, bx.rgb, by.rg) and an 8-B record
-// (by.b, bxy.rgb).  Values are in byte units (0..255).
-__device__ __forceinline__ float2 h2f(unsigned u);
-
-struct Coef8 {
-    float a[3], bx[3], by[3], bxy[3];
-    __device__ __forceinline__ void load(const void *tex, long long idx, long long npx)
-    {
-        const uint4 q = __ldg((const uint4 *)tex + idx);
-        const uint2 e = __ldg((const uint2 *)((const uint4 *)tex + npx) + idx);
-        float2 t;
-        t = h2f(q.x); a[0] = t.x; a[1] = t.y;
-        t = h2f(q.y); a[2] = t.x; bx[0] = t.y;
-        t = h2f(q.z); bx[1] = t.x; bx[2] = t.y;
-        t = h2f(q.w); by[0] = t.x; by[1] = t.y;
-        t = h2f(e.x); by[2] = t.x; bxy[0] = t.y;
-        t = h2f(e.y); bxy[1] = t.x; bxy[2] = t.y;
-    }
-};
+// The sampling texture's storage format: RGBA8 views keep their texels as
+// IEEE halves (integers 0..255 are exact), laid out as the FP16 texture;
+// values are in byte units (0..255).
+template <int FMT>
+__host__ __device__ constexpr int tex_fmt() { return FMT == LFD_RGBA8 ? LFD_RGBA_F16 : FMT; }
 
 __device__ __forceinline__ float2 h2f(unsigned u)
 {
@@ -137,15 +119,9 @@ template <int FMT>
 __device__ __forceinline__ float3 texel_colour(const void *tex, int x, int y, int W, int H)
 {
     const long long idx = quad_index(x, y, W), npx = quad_entries(W, H);
-    if constexpr (FMT == LFD_RGBA8) {
-        const uint4 q = __ldg((const uint4 *)tex + idx);
-        const float2 t0 = h2f(q.x), t1 = h2f(q.y);
-        return make_float3(t0.x, t0.y, t1.x);
-    } else {
-        Quad<FMT> q;
-        q.load(tex, idx, npx);
-        return make_float3(q.rg[0].x, q.rg[0].y, q.b02.x);
-    }
+    Quad<tex_fmt<FMT>()> q;
+    q.load(tex, idx, npx);
+    return make_float3(q.rg[0].x, q.rg[0].y, q.b02.x);
 }
 
 // Truncated SSD of Eq. 1 between the reference colour `ref` and the bilinear
@@ -156,26 +132,19 @@ template <int FMT>
 __device__ __forceinline__ float tssd_quad(const void *tex, long long idx, long long npx, float fx, float fy,
                                            float3 ref, float T)
 {
-    if constexpr (FMT == LFD_RGBA8) {
-        Coef8 q;
-        q.load(tex, idx, npx);
-        const float fxy = fx * fy;
-        const float dr = ref.x - fmaf(fxy, q.bxy[0], fmaf(fy, q.by[0], fmaf(fx, q.bx[0], q.a[0])));
-        const float dg = ref.y - fmaf(fxy, q.bxy[1], fmaf(fy, q.by[1], fmaf(fx, q.bx[1], q.a[1])));
-        const float db = ref.z - fmaf(fxy, q.bxy[2], fmaf(fy, q.by[2], fmaf(fx, q.bx[2], q.a[2])));
-        return fminf(fmaf(dr, dr, fmaf(dg, dg, db * db)), T);
-    } else if constexpr (FMT == LFD_RGBA_F16 || FMT == LFD_RGBA_BF16) {
+    constexpr int TF = tex_fmt<FMT>();
+    if constexpr (TF == LFD_RGBA_F16 || TF == LFD_RGBA_BF16) {
         // the record's words as they are: the first texel of each x lerp
         // converted, the second entering through the mixed-precision
         // subtraction; the same values as the Quad form below
         const uint4 a = __ldg((const uint4 *)tex + idx);
         const uint2 e = __ldg((const uint2 *)((const uint4 *)tex + npx) + idx);
         const float2 FX = dup2(fx);
-        const float2 r0 = cvt2<FMT>(a.x), r2 = cvt2<FMT>(a.z), b02 = cvt2<FMT>(e.x);
-        const float2 top = ffma2(FX, msub2<FMT>(a.y, r0), r0);
-        const float2 bot = ffma2(FX, msub2<FMT>(a.w, r2), r2);
+        const float2 r0 = cvt2<TF>(a.x), r2 = cvt2<TF>(a.z), b02 = cvt2<TF>(e.x);
+        const float2 top = ffma2(FX, msub2<TF>(a.y, r0), r0);
+        const float2 bot = ffma2(FX, msub2<TF>(a.w, r2), r2);
         const float2 rg = ffma2(dup2(fy), fsub2(bot, top), top);
-        const float2 bb = ffma2(FX, msub2<FMT>(e.y, b02), b02);       // (top, bottom) blue
+        const float2 bb = ffma2(FX, msub2<TF>(e.y, b02), b02);        // (top, bottom) blue
         const float2 d = fsub2(make_float2(ref.x, ref.y), rg);
         const float2 d2 = fmul2(d, d);
         const float db = ref.z - fmaf(fy, bb.y - bb.x, bb.x);
