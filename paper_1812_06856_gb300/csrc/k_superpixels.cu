@@ -377,13 +377,14 @@ cudaError_t launch_quads(const Workspace &w, int V, int max_px, int fmt, cudaStr
 //    of every view, so the rows of the sampling textures and rasterised maps
 //    they gather from (their own band, shifted by the disparity, in each
 //    neighbour view) stay in L2 together instead of spanning whole views.
-//    The sweep's order is finally partitioned, stably, by the label-count
-//    class of each superpixel's light field (mode 2): one sweep launch per
-//    class, its CTAs as wide as the class's label count.
+//    The sweep's order is finally partitioned, stably, by sweep class (mode
+//    2: the label-count class of each superpixel's light field and the pair
+//    form of its view): one sweep launch per class, its CTAs as wide as the
+//    class's label count, compiled for the class's pair form.
 
 __device__ __forceinline__ int order_key(const Workspace &w, int gs, int mode, int bands)
 {
-    if (mode == 2) return w.views[__ldg(w.sp_view + gs)].lclass;
+    if (mode == 2) return w.views[__ldg(w.sp_view + gs)].sclass;
     const int n = __ldg(w.sp_cnt + gs);
     const int cls = mode == 0 ? (n + 31) >> 5 : 31 - __clz(max(n, 1));
     const ViewDev &vd = w.views[__ldg(w.sp_view + gs)];

@@ -243,7 +243,7 @@ struct lfd_ctx {
     cudaEvent_t ev_bdepth = nullptr;
     uint64_t tuned_sig = 0;
     // sweep launches: superpixels of label-count class c at order_sweep[cls_base[c] ..+ cls_count[c])
-    int cls_base[LCLASSES] = {}, cls_count[LCLASSES] = {};
+    int cls_base[NSCLASS] = {}, cls_count[NSCLASS] = {};
 };
 
 namespace {
@@ -368,7 +368,7 @@ void view_params(ViewDev &d, const lfd_params &p, int fmt, int lf)
     d.xy_hi = (float)(1.0 + p.xy_eps);
     d.perturb_k = p.perturb_samples;
     d.perturb_scale = p.perturb_scale;
-    d.lclass = label_class(p.num_labels);
+    d.sclass = 3 * label_class(p.num_labels);   // the pair form is added once the pairs are known
 }
 
 lfd_status ensure_pinned(lfd_ctx *ctx, size_t bytes)
@@ -529,7 +529,7 @@ lfd_status plan_workspace(lfd_ctx *ctx, int n, const lfd_lightfield *lfs)
     ctx->d_order = (int *)a.take(4 * S);
     ctx->d_order_sweep = (int *)a.take(4 * S);
     ctx->d_hist = (int *)a.take(4 * ORDER_KEYS_HOST);
-    ctx->d_queue = (int *)a.take(64);
+    ctx->d_queue = (int *)a.take(4 * QUEUE_INTS);
     ctx->d_depth_ptrs = (float **)a.take(sizeof(float *) * V);
     ctx->d_planesA = (float4 *)a.take(16 * S);
     ctx->d_planesB = (float4 *)a.take(16 * S);
@@ -698,27 +698,32 @@ lfd_status plan_input(lfd_ctx *ctx, int n, const lfd_lightfield *lfs, const lfd_
     // translation pairs: affine with P's upper 2 x 2 block = P22 I to within
     // 1e-12 relative (rectified cameras with equal intrinsics): a pixel offset
     // du < 2^16 then moves by less than 1e-7 px against the exact homography
+    // The propagation takes one form for the whole input, the sweep one per
+    // view (its sweep class), so that a batch of mixed rigs sweeps each view
+    // with the form of its own pairs.
     int affine = 1, shift = 1;
-    for (int v = 0; v < V; v++)
+    for (int v = 0; v < V; v++) {
+        int aff_v = 1, shift_v = 1;
         for (int k = 0; k < LFD_MAXN; k++) {
             if (ctx->nbr[(size_t)v * LFD_MAXN + k] < 0) continue;
             const PairDev &pd = hp[v * LFD_MAXN + k];
-            if (pd.P[6] != 0.0 || pd.P[7] != 0.0 || pd.q[2] != 0.0) affine = 0;
+            if (pd.P[6] != 0.0 || pd.P[7] != 0.0 || pd.q[2] != 0.0) aff_v = 0;
             const double e = 1e-12 * std::fabs(pd.P[8]);
             if (!(pd.P[8] > 0.0) || std::fabs(pd.P[0] - pd.P[8]) > e || std::fabs(pd.P[4] - pd.P[8]) > e ||
                 std::fabs(pd.P[1]) > e || std::fabs(pd.P[3]) > e)
-                shift = 0;
+                shift_v = 0;
         }
+        const int pf = std::min(aff_v ? (shift_v ? 2 : 1) : 0, ctx->max_pair_form);
+        hv[v].sclass += ctx->c.sweep_frame ? 0 : pf;     // world-frame sweeps: general form
+        affine &= aff_v;
+        shift &= shift_v;
+    }
     ctx->c.affine = affine && ctx->max_pair_form >= 1;
     ctx->c.shift = affine && shift && ctx->max_pair_form >= 2;
-    // the sweep order is partitioned by label-count class, classes ascending
-    for (int k = 0; k < LCLASSES; k++) ctx->cls_count[k] = 0;
-    for (const LfInfo &l : ctx->lfs) {
-        int S_l = 0;
-        for (int v = 0; v < l.V; v++) S_l += L.S[l.first_view + v];
-        ctx->cls_count[label_class(l.p.num_labels)] += S_l;
-    }
-    for (int k = 0, b = 0; k < LCLASSES; k++) {
+    // the sweep order is partitioned by sweep class, classes ascending
+    for (int k = 0; k < NSCLASS; k++) ctx->cls_count[k] = 0;
+    for (int v = 0; v < V; v++) ctx->cls_count[hv[v].sclass] += L.S[v];
+    for (int k = 0, b = 0; k < NSCLASS; k++) {
         ctx->cls_base[k] = b;
         b += ctx->cls_count[k];
     }
@@ -733,7 +738,7 @@ lfd_status build_orders(lfd_ctx *ctx, cudaStream_t st)
 {
     const int bands = ctx->lc.order_bands;
     int classes = 0;
-    for (int k = 0; k < LCLASSES; k++) classes += ctx->cls_count[k] > 0;
+    for (int k = 0; k < NSCLASS; k++) classes += ctx->cls_count[k] > 0;
     if (classes > 1) {
         LFD_CUDA(traced(ctx, LFD_STAGE_SUPERPIXELS, st, [&] {
             return launch_sp_order(ctx->w, ctx->d_order, ctx->d_hist, 1, bands, nullptr, st);
@@ -861,16 +866,19 @@ lfd_status rasterize_state(lfd_ctx *ctx, const float4 *planes, float *const *dep
     return LFD_OK;
 }
 
-// One sweep launch per label-count class present, CTAs as wide as the class
-// (at most lc.sweep_threads).
+// One sweep launch per sweep class present (label-count class x pair form),
+// CTAs as wide as the class's label count (at most lc.sweep_threads).
 lfd_status run_sweep(lfd_ctx *ctx, float *cost, cudaStream_t st)
 {
-    if (ctx->lc.sweep_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 64, st));
-    for (int k = 0; k < LCLASSES; k++) {
+    if (ctx->lc.sweep_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 4 * QUEUE_INTS, st));
+    for (int k = 0; k < NSCLASS; k++) {
         if (!ctx->cls_count[k]) continue;
-        const int threads = std::min(LCLASS_THREADS[k], ctx->lc.sweep_threads);
+        const int threads = std::min(LCLASS_THREADS[k / 3], ctx->lc.sweep_threads);
+        Consts c = ctx->c;                   // the class's pair form
+        c.affine = k % 3 >= 1;
+        c.shift = k % 3 == 2;
         LFD_CUDA(traced(ctx, LFD_STAGE_SWEEP, st, [&] {
-            return launch_sweep(ctx->w, ctx->c, ctx->lc, threads, ctx->cls_base[k], ctx->cls_count[k], 4 + k,
+            return launch_sweep(ctx->w, c, ctx->lc, threads, ctx->cls_base[k], ctx->cls_count[k], 4 + k,
                                 ctx->d_planesA, ctx->d_label, cost, st);
         }));
     }
@@ -884,7 +892,7 @@ lfd_status iterate_flat(lfd_ctx *ctx, int iter, const float4 *in, float4 *out, i
 {
     lfd_status s;
     if ((s = rasterize_state(ctx, in, nullptr, st)) != LFD_OK) return s;
-    if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 64, st));
+    if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 4 * QUEUE_INTS, st));
     Consts c = ctx->c;
     c.batch_iters = frame ? 1 : 0;
     LFD_CUDA(traced(ctx, LFD_STAGE_PROPAGATE, st, [&] {
@@ -1012,7 +1020,7 @@ lfd_status autotune(lfd_ctx *ctx, cudaStream_t st)
                     // iteration index, and a shape can win on the first and lose on the rest
                     auto fn = [&]() -> lfd_status {
                         for (int it : {1, it_last}) {
-                            if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 64, st));
+                            if (ctx->lc.prop_persistent) LFD_CUDA(cudaMemsetAsync(ctx->d_queue, 0, 4 * QUEUE_INTS, st));
                             LFD_CUDA(launch_propagate(ctx->w, ctx->c, ctx->lc, it, ctx->d_planesA, ctx->d_planesB,
                                                       nullptr, nullptr, st));
                             if (it_last == 1) break;

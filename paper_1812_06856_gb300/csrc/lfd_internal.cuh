@@ -58,7 +58,8 @@ struct ViewDev {
     float col_gain;          // sqrt(k_col): scale of the colours in the rasterised maps
     float dep_gain;          // sqrt(k_sig): scale of their depth values
     int perturb_k;           // perturbation samples of the refinement (flagged variant; 0 = off)
-    int lclass;              // label-count class of its light field (sweep CTA width, LCLASS_THREADS)
+    int sclass;              // sweep class: label-count class of its light field x 3 + the pair form of
+                             // its neighbour pairs (0 general, 1 affine, 2 translation), see NSCLASS
     double perturb_scale;    // their relative radius at I = 1
 };
 
@@ -117,7 +118,7 @@ struct Workspace {
     DevCounters *ctr;
     const int *order;        // [S_total] work order: descending pixel-slot class, index order inside
     const int *order_sweep;  // [S_total] sweep work order: descending power-of-two size class, index order inside
-    int *queue;              // [16] work-queue counters of persistent launches
+    int *queue;              // [32] work-queue counters of persistent launches
     int S_total;
     long long px_total;
 };
@@ -275,6 +276,10 @@ constexpr int ORDER_KEYS = ORDER_CLASSES * ORDER_BANDS;
 // several passes), so that few threads idle when L is not a multiple of 256.
 constexpr int LCLASSES = 6;
 constexpr int LCLASS_THREADS[LCLASSES] = {64, 128, 160, 192, 224, 256};
+// sweep classes: one sweep launch per (label-count class, pair form) present,
+// so that each view of a batch of mixed rigs sweeps with its own pair form
+constexpr int NSCLASS = LCLASSES * 3;
+constexpr int QUEUE_INTS = 32;          // 4 + NSCLASS <= QUEUE_INTS
 inline int label_class(int L)
 {
     for (int c = 0; c < LCLASSES; c++)
