@@ -221,7 +221,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        sm, smax, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -232,11 +232,16 @@ class ClockSampler:
                 smax.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(parts[3]))
+            except ValueError:
+                pass
             for nm, val in zip(names, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w": statistics.median(pw) if pw else None}
 
 
 def measured_peaks() -> dict:
@@ -463,6 +468,9 @@ def measure_frames(cfg: int, args, dev: str, local: int, ws: int, l2_peak: float
             ctx_h.estimate_host(vh, lh, K, R, t, GW, GH, params, ph, dh)
         ctx_h.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        eclocks = ClockSampler(local)
+        eclocks.start()
+        time.sleep(0.3)
         barrier()
         for k in range(args.steps):
             flush.fill_(k & 0xff)
@@ -470,11 +478,14 @@ def measure_frames(cfg: int, args, dev: str, local: int, ws: int, l2_peak: float
             ctx_h.estimate_host(vh, lh, K, R, t, GW, GH, params, ph, dh)
             evs[k][1].record(stream)
         barrier()
+        e2e_clocks = eclocks.stop()
         e_ms, e_value = replica_reduce(float(np.mean([a.elapsed_time(b) for a, b in evs])), hyp_step, ws, dev)
         res["e2e"] = {"value": e_value, "unit": UNIT,
                       "h2d_bytes_per_step": int(vh.numel() * vh.element_size() + lh.numel() * 4),
                       "d2h_bytes_per_step": int(ph.numel() * 4 + dh.numel() * 4), "ms_per_step": e_ms,
-                      "ms_per_view": e_ms / V}
+                      "ms_per_view": e_ms / V, "step_ms_min_max": [float(min(a.elapsed_time(b) for a, b in evs)),
+                                                                    float(max(a.elapsed_time(b) for a, b in evs))],
+                      "clocks": e2e_clocks}
         ctx_h.close()
         del vh, lh, ph, dh
     ctx.close()
