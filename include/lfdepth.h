@@ -381,9 +381,11 @@ lfd_status lfd_launch_config(const lfd_ctx *ctx, int32_t *out);
  *   2 translation: affine and P's upper 2 x 2 block = P22 I to 1e-12
  *                  (rectified cameras with equal intrinsics): a
  *                  fronto-parallel sweep plane moves every pixel by one
- *                  vector; the sweep's costs differ from the general form's by
- *                  FP32 rounding of the sample position only (the
- *                  propagation uses form 1).
+ *                  vector, whose integer part and fraction the sweep takes in
+ *                  FP64; its costs differ from the general form's by the
+ *                  rounding of the sample position only (the general form
+ *                  rounds absolute positions to FP32; the propagation uses
+ *                  form 1).
  * lfd_set_pair_forms(ctx, max_form): the largest form the context may use
  * for inputs bound after the call (0, 1 or 2; default 2; LFD_ERR_INVALID_ARG
  * otherwise); drops a captured CUDA graph.

@@ -47,6 +47,7 @@ struct SweepPair {
     double pref[3];                       // P (ref,1) in FP64
     double q[3];
     double p0[3], p1[3];                  // columns 0,1 of P in FP64 (world-frame sweeps)
+    double icw;                           // 1 / P (ref,1)_z (translation pairs: every label's w)
     const void *tex;
 };
 
@@ -123,6 +124,7 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
             sp.p0[r] = pd.P[3 * r];
             sp.p1[r] = pd.P[3 * r + 1];
         }
+        sp.icw = sp.pref[2] > 0.0 ? 1.0 / sp.pref[2] : 0.0;
         sp.tex = pd.quad_i;
         sh.pair[threadIdx.x] = sp;
     }
@@ -203,13 +205,17 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
                     // with ix = du + floor(X0) and fx = X0 - floor(X0) the texture-area
                     // test -1/2 <= ix + fx < Wi - 1/2 is lo <= ix <= lo + Wi - 1, lo = -1
                     // when fx >= 1/2 and 0 otherwise (the same for y)
+                    // The shift (X0, Y0) = (cx, cy) / w is split into its integer part and
+                    // its fraction in FP64 (w = P (ref,1)_z for every label: q_z = 0), so
+                    // the fraction is exact to FP32 rounding of a number below 1 whatever
+                    // the image size (an absolute FP32 position near x = 2000 would carry
+                    // ~1e-4 px).
                     const float4 *xyw = sh.xyw[WORLD ? 0 : j];
-                    const float rw = rcp_approx(cw);
-                    const float X0 = cx * rw, Y0 = cy * rw;
-                    if (cw > 0.f && fabsf(X0) < 1e9f && fabsf(Y0) < 1e9f) {
-                        const float xf = floorf(X0), yf = floorf(Y0);
-                        const float fx = X0 - xf, fy = Y0 - yf;
-                        const int ixk = (int)xf, iyk = (int)yf;
+                    const double X0 = fma(zq0, sh.gh[3], sp.pref[0]) * sp.icw;
+                    const double Y0 = fma(zq1, sh.gh[3], sp.pref[1]) * sp.icw;
+                    if (sp.icw > 0.0 && fabs(X0) < 1e9 && fabs(Y0) < 1e9) {
+                        const int ixk = __double2int_rd(X0), iyk = __double2int_rd(Y0);
+                        const float fx = (float)(X0 - (double)ixk), fy = (float)(Y0 - (double)iyk);
                         const int ox = ixk + (fx >= 0.5f ? 1 : 0), oy = iyk + (fy >= 0.5f ? 1 : 0);
                         const unsigned spx = (unsigned)(Wi - 1), spy = (unsigned)(Hi - 1);
                         const long long koff = quad_index(ixk, iyk, Wi), npx = quad_entries(Wi, Hi);

@@ -449,6 +449,37 @@ def test_config2_full_size_sampled_state_injected(lfd):
     assert adm2.all() and rep["identical_when_decided"] == 1.0 and rep["depth_within_0p5pct"] == 1.0
 
 
+def test_config3_full_size_sampled_state_injected(lfd):
+    """The headline frame at full size (16 x 1920x1080 FP16, 256 labels; the
+    translation-pair sweep of the 4 x 4 grid) in the launch configuration the
+    bench times; the oracle scores a deterministic sample of superpixels on
+    the same FP16 colours, the sweep and a state-injected iteration 1."""
+    lf = synth.make_config(3, device="cuda")
+    views, labels, rgb = PT.gpu_inputs(lf, "rgba_f16")
+    params = synth.method_params(lf)
+    ctx = bind(lfd, lf, views, labels, params)
+    assert ctx.pair_form() == 2
+    planes, lab, costs = ctx.plane_sweep(want_labels=True, want_costs=True)
+    ctx.synchronize()
+    o = PT.make_oracle(lf, rgb, params)
+    rng = np.random.default_rng(3)
+    items = np.sort(rng.choice(o.S_total, size=40, replace=False)).astype(np.int32)
+    sw = o.sweep(items, want_costs=True)
+    c = costs.cpu().numpy().astype(np.float64)[items]
+    ok = PT.within(c, sw["cost_lo"], sw["cost_hi"], absf=PT.tssd_abs_floor(o, items)[:, None] + PT.ABS)
+    labg = lab.cpu().numpy()[items]
+    adm = [labg[i] == sw["label"][i] or PT.admissible(-sw["cost_lo"][i, labg[i]], -sw["cost_hi"][i])
+           for i in range(len(items)) if sw["label"][i] >= 0]
+    print(f"config3 sweep sample: costs ok {ok.mean():.5f} labels identical "
+          f"{np.mean(labg == sw['label']):.4f} admissible {np.mean(adm):.4f}")
+    assert ok.all() and all(adm)
+    state = planes.cpu().numpy()
+    rep = {}
+    out, same, adm2 = _iterate_compare(lfd, ctx, o, state, 1, items[:20], rep)
+    print("config3 iteration 1 sample:", rep)
+    assert adm2.all() and rep["identical_when_decided"] == 1.0 and rep["depth_within_0p5pct"] == 1.0
+
+
 # ---------------------------------------------------------------------------
 # boundary behaviour
 # ---------------------------------------------------------------------------
