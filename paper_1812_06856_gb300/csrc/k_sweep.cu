@@ -162,10 +162,19 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
                     const SweepPair &sp = sh.pair[j];
                     const float2 d = sh.d[i];
                     if (PF == PF_SHIFT) {
-                        // the pixel offset and its offset in view j's sampling texture
+                        // the pixel offset and, for 16-bit textures, the pixel's colour in
+                        // the texture's format (one broadcast per sample instead of two),
+                        // else its offset in view j's sampling texture
                         const int du = (int)d.x, dv = (int)d.y;
-                        sh.xyw[j][i] = make_float4(__int_as_float(du), __int_as_float(dv),
-                                                   __int_as_float(dv * (sp.Wi + 1) + du), 0.f);
+                        if constexpr (tex_fmt<FMT>() != LFD_RGBA_F32) {
+                            const float4 rc = sh.ref[i];
+                            sh.xyw[j][i] = make_float4(__int_as_float(du), __int_as_float(dv),
+                                                       __uint_as_float(pack2<tex_fmt<FMT>()>(rc.x, rc.y)),
+                                                       __uint_as_float(pack2<tex_fmt<FMT>()>(rc.z, 0.f)));
+                        } else {
+                            sh.xyw[j][i] = make_float4(__int_as_float(du), __int_as_float(dv),
+                                                       __int_as_float(dv * (sp.Wi + 1) + du), 0.f);
+                        }
                     } else {
                         sh.xyw[j][i] = make_float4(fmaf(sp.a00, d.x, sp.a01 * d.y), fmaf(sp.a10, d.x, sp.a11 * d.y),
                                                    fmaf(sp.a20, d.x, sp.a21 * d.y), 0.f);
@@ -222,12 +231,19 @@ __device__ __forceinline__ void sweep_sp(const Workspace &w, const Consts &c, in
 #pragma unroll 4
                         for (int i = 0; i < cn; i++) {
                             const float4 q = xyw[i];
-                            const float4 rc = sh.ref[i];
-                            const bool in = (unsigned)(__float_as_int(q.x) + ox) <= spx &&
-                                            (unsigned)(__float_as_int(q.y) + oy) <= spy;
+                            const int du = __float_as_int(q.x), dv = __float_as_int(q.y);
+                            const bool in = (unsigned)(du + ox) <= spx && (unsigned)(dv + oy) <= spy;
                             // branch-free: a sample off the texture area reads entry 0
-                            const long long e = in ? koff + __float_as_int(q.z) : 0;
-                            const float t = tssd_quad<FMT>(tex, e, npx, fx, fy, make_float3(rc.x, rc.y, rc.z), T);
+                            float t;
+                            if constexpr (tex_fmt<FMT>() != LFD_RGBA_F32) {
+                                const long long e = in ? koff + (dv * (Wi + 1) + du) : 0;
+                                t = tssd_quad_href<FMT>(tex, e, npx, fx, fy, __float_as_uint(q.z),
+                                                        __float_as_uint(q.w), T);
+                            } else {
+                                const float4 rc = sh.ref[i];
+                                const long long e = in ? koff + __float_as_int(q.z) : 0;
+                                t = tssd_quad<FMT>(tex, e, npx, fx, fy, make_float3(rc.x, rc.y, rc.z), T);
+                            }
                             cost += in ? t : T;
                         }
                     } else {

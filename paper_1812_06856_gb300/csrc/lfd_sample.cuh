@@ -98,6 +98,33 @@ __device__ __forceinline__ float2 msub2(unsigned w, float2 a)
     return d;
 }
 
+// float(lo(w)) - a for a word w holding a FP16 or BF16 value in its low half
+template <int FMT>
+__device__ __forceinline__ float msub1(unsigned w, float a)
+{
+    float d;
+    if constexpr (FMT == LFD_RGBA_F16)
+        asm("{\n\t.reg .f16 l, h;\n\tmov.b32 {l, h}, %1;\n\tsub.rn.f32.f16 %0, l, %2;\n\t}"
+            : "=f"(d) : "r"(w), "f"(a));
+    else
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\tsub.rn.f32.bf16 %0, l, %2;\n\t}"
+            : "=f"(d) : "r"(w), "f"(a));
+    return d;
+}
+
+// (lo, hi) packed as the texture's 16-bit format (exact for its own texel values)
+template <int FMT>
+__device__ __forceinline__ unsigned pack2(float lo, float hi)
+{
+    if constexpr (FMT == LFD_RGBA_F16) {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<unsigned *>(&h);
+    } else {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<unsigned *>(&h);
+    }
+}
+
 template <int FMT>
 __device__ __forceinline__ float2 cvt2(unsigned w)
 {
@@ -164,6 +191,30 @@ __device__ __forceinline__ float tssd_quad(const void *tex, long long idx, long 
         const float db = ref.z - fmaf(fy, bb.y - bb.x, bb.x);
         return fminf(fmaf(db, db, d2.x + d2.y), T);
     }
+}
+
+// tssd_quad for a 16-bit texture with the reference colour given in the
+// texture's own format (ref_rg: red|green, ref_b: blue in the low half):
+// the reference enters the differences through the mixed-precision
+// subtraction, the same values as tssd_quad on the converted colour.
+template <int FMT>
+__device__ __forceinline__ float tssd_quad_href(const void *tex, long long idx, long long npx, float fx, float fy,
+                                                unsigned ref_rg, unsigned ref_b, float T)
+{
+    constexpr int TF = tex_fmt<FMT>();
+    static_assert(TF == LFD_RGBA_F16 || TF == LFD_RGBA_BF16, "16-bit textures only");
+    const uint4 a = __ldg((const uint4 *)tex + idx);
+    const uint2 e = __ldg((const uint2 *)((const uint4 *)tex + npx) + idx);
+    const float2 FX = dup2(fx);
+    const float2 r0 = cvt2<TF>(a.x), r2 = cvt2<TF>(a.z), b02 = cvt2<TF>(e.x);
+    const float2 top = ffma2(FX, msub2<TF>(a.y, r0), r0);
+    const float2 bot = ffma2(FX, msub2<TF>(a.w, r2), r2);
+    const float2 rg = ffma2(dup2(fy), fsub2(bot, top), top);
+    const float2 bb = ffma2(FX, msub2<TF>(e.y, b02), b02);        // (top, bottom) blue
+    const float2 d = msub2<TF>(ref_rg, rg);
+    const float2 d2 = fmul2(d, d);
+    const float db = msub1<TF>(ref_b, fmaf(fy, bb.y - bb.x, bb.x));
+    return fminf(fmaf(db, db, d2.x + d2.y), T);
 }
 
 // Truncated SSD of Eq. 1 between the reference colour `ref` and view i sampled
